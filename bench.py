@@ -1,0 +1,354 @@
+"""Benchmark of the Arnold-web scan hot path on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Workload (the FP64 Arnold-web scan): a 2048 x 2048 grid of initial actions
+(p_x, p_y) at E = 400 (eps_eff = 0.005, the paper's weak-perturbation value),
+eps = 1, h = 0.01 T, sixth-order Yoshida composition, tangent vector on,
+renormalised every 100 steps.  The scan runs 1e6 composite steps; one bench
+step advances the whole grid by --chunk composite steps (default 250) and
+writes the indicator fields (FTLE, class, V, sampled dE) and the ensemble
+statistics, as a scan does at each output point.  The metric is map-steps/s
+(one map step = one composite step of one trajectory, tangent included).
+The state (~0.9 GB) is far larger than L2, so no flush is needed.
+
+Under torchrun (N > 1) each rank scans its own 2048 x 2048 grid (seed =
+rank): independent problems, no collective on the data path, weak scaling.
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "map-steps/s (with tangent) and % of FP pipe peak; FP32-comp vs FP64 at equal indicator agreement"
+G, E, EPS = 2048, 400.0, 1.0
+H = 0.02 * math.pi
+HORIZON = 1_000_000
+# FP64 instructions and FLOPs (FMA = 2) per composite step, counted from the
+# kernel source (iterate_fp64.cu, devmath.cuh) for Yoshida-6A with tangent:
+# kick = 3 sincos (10 instr / 16 flop each) + force (8 / 11) + tangent (14 / 22),
+# drift = 6 FMA (6 / 12); 7 kicks + 8 drifts.
+FP64_INSTR_PER_STEP = 7 * (3 * 10 + 8 + 14) + 8 * 6
+FP64_FLOP_PER_STEP = 7 * (3 * 16 + 11 + 22) + 8 * 12
+# FP32C: FP32-pipe instructions per composite step (iterate_fp32c.cu): kick =
+# 3 sincos (10 each) + force with TwoSum adds (5 + 3 + 3 * 7) + tangent (14);
+# drift = 3 * (4 product + 6 TwoSum + 2) + 3 tangent; 6 Fast2Sum renormalisations.
+FP32C_INSTR_PER_STEP = 7 * (3 * 10 + 29 + 14) + 8 * (3 * 12 + 3) + 6 * 3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=int(os.environ.get("WORLD_SIZE", "1")))
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--chunk", type=int, default=250, help="composite steps per bench step")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp32c", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks ---
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ CPU oracle ---
+def cpu_oracle_rate(seconds: float, cells: int = 512):
+    """The FP64 oracle as it stands, on all host cores (one trajectory range per
+    thread; ctypes releases the GIL), over sampled cells of the same grid."""
+    import oracle
+    from paper_1107_4107_b300 import inputs
+    cores = os.cpu_count() or 1
+    idx = inputs.sample_cells(G * G, cells, seed=7)
+    X, Pxy = inputs.grid_slice(G, E, EPS, seed=0)
+    X, Pxy = X[:, idx].copy(), Pxy[:, idx].copy()
+    P = np.zeros((3, cells)); P[:2] = Pxy
+    P = oracle.pz_from_energy(E, EPS, X, P)
+    st = oracle.State(X, P, oracle.Params(eps=EPS, h=H, renorm_every=100))
+    t0 = time.perf_counter()
+    st.advance(20, threads=cores)
+    dt = time.perf_counter() - t0
+    steps = max(20, int(seconds / max(dt, 1e-6) * 20))
+    t0 = time.perf_counter()
+    st.advance(steps, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": cells * steps / dt, "unit": "map-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cells} sampled cells of the 2048x2048 E=400 grid x {steps} composite steps "
+                      f"(tangent on), FP64, {dt:.1f} s"}
+
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return
+    per = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_oracle_rate(per / 4, cells=128)
+    vals = []
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_oracle_rate(per, cells=256))
+    wall = time.perf_counter() - t_all
+    v = statistics.mean(r["value"] for r in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "map-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config(args),
+            "cpu_baseline": {"value": v, "unit": "map-steps/s", "cores": vals[0]["cores"], "kind": "oracle",
+                             "sample": vals[0]["sample"] + f"; mean of {args.steps} samples"},
+            "e2e": {"value": v, "unit": "map-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config(args):
+    return {"workload": "FP64 Arnold-web scan, 2048x2048 grid of initial actions (p_x, p_y), E=400 "
+                        "(eps_eff=0.005), eps=1, h=0.01T, Yoshida-6A, tangent renormalised every 100 steps, "
+                        f"1e6-step scan timed in chunks of {args.chunk} steps",
+            "grid": G, "n_traj": G * G, "E": E, "eps": EPS, "h": H, "scheme": "yoshida6a", "precision": "fp64",
+            "steps_per_bench_step": args.chunk, "scan_horizon": HORIZON, "global_batch": G * G * args.gpus,
+            "parallelism": f"independent scans x{args.gpus}", "l2": "state 0.9 GB > 126 MB L2 (no flush needed)"}
+
+
+# ------------------------------------------------------------------ ours ---
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import torch
+    from paper_1107_4107_b300.api import ArnoldEnsemble, probe_peak
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream()
+    n = G * G
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # peaks of this GPU, measured live (FP64 pipe, FP32 pipe)
+    dfma = probe_peak("dfma", local)
+    ffma = probe_peak("ffma", local)
+
+    ens = ArnoldEnsemble(n, precision="fp64", device=local, stream=stream.cuda_stream)
+    ens.init_grid(G, E, seed=rank)
+    chi = torch.empty(n, device="cuda", dtype=torch.float64)
+    V = torch.empty((3, n), device="cuda", dtype=torch.float64)
+    dEm = torch.empty(n, device="cuda", dtype=torch.float64)
+    cls = torch.empty(n, device="cuda", dtype=torch.uint8)
+
+    it_ms = []
+
+    def one_step(timed=False):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ens.iterate(args.chunk)
+        e1.record(stream)
+        ens.indicator("chi", out=chi)
+        ens.indicator("class", out=cls)
+        ens.indicator("V", out=V)
+        ens.indicator("dE_max", out=dEm)
+        s = ens.stats()
+        if timed:
+            it_ms.append((e0, e1))
+        return s
+
+    lw = ens.launches
+    ens.iterate(args.chunk)
+    launches_per_iterate = ens.launches - lw
+    for _ in range(args.warmup):
+        one_step()
+    barrier()
+    l0 = ens.launches
+    with ClockSampler(local) as clk:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            one_step(timed=True)
+        t1.record(stream)
+        barrier()
+    ms = t0.elapsed_time(t1)
+    gpu_launches = ens.launches - l0
+    if dist:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    total_steps = n * args.chunk * args.steps * world
+    value = total_steps / (ms * 1e-3)
+    iter_ms = sum(a.elapsed_time(b) for a, b in it_ms) / len(it_ms)
+    per_launch_ms = iter_ms / launches_per_iterate
+    map_steps_per_launch = n * args.chunk / launches_per_iterate
+    achieved_flops = map_steps_per_launch * FP64_FLOP_PER_STEP / (per_launch_ms * 1e-3)
+    pipe_instr = map_steps_per_launch * FP64_INSTR_PER_STEP / (per_launch_ms * 1e-3)
+    roofline = {"bound": "alu", "kernel": "k_iterate_fp64<7,true>",
+                "achieved": achieved_flops / 1e12, "peak": 2 * dfma / 1e12, "unit": "TFLOP/s",
+                "frac": achieved_flops / (2 * dfma), "traffic": traffic_for("k_iterate_fp64"),
+                "peak_source": "measured live: DFMA probe (arnold_probe_peak), FMA = 2 FLOP",
+                "fp64_pipe_frac": pipe_instr / dfma,
+                "flop_per_map_step": FP64_FLOP_PER_STEP, "fp64_instr_per_map_step": FP64_INSTR_PER_STEP}
+
+    # ---- end to end through the C ABI with host buffers (pinned) ----
+    e2e = None
+    if rank == 0 or world > 1:
+        raw = torch.empty((6, n), device="cuda", dtype=torch.float64)
+        ens2 = ArnoldEnsemble(n, precision="fp64", device=local, stream=stream.cuda_stream)
+        ens2.init_grid(G, E, seed=rank, raw_out=raw)
+        hx = raw[:3].cpu().pin_memory()
+        hp = raw[3:].cpu().pin_memory()
+        hchi = torch.empty(n, dtype=torch.float64).pin_memory()
+        k2 = max(2, args.steps // 3)
+
+        def e2e_step():
+            ens2.set_state(hx, hp)
+            ens2.iterate(args.chunk)
+            ens2.indicator("chi", out=hchi)
+
+        e2e_step()
+        barrier()
+        w0 = time.perf_counter()
+        for _ in range(k2):
+            e2e_step()
+        barrier()
+        wt = time.perf_counter() - w0
+        e2e = {"value": n * args.chunk * k2 * world / wt, "unit": "map-steps/s",
+               "h2d_bytes_per_step": int(hx.numel() * 8 + hp.numel() * 8), "d2h_bytes_per_step": int(hchi.numel() * 8),
+               "steps": k2, "api": "ArnoldEnsemble.set_state/iterate/indicator (C ABI, host pinned buffers)"}
+        ens2.close()
+
+    # ---- FP32C (compensated) on the same workload ----
+    fp32c = None
+    if not args.no_fp32c:
+        e3 = ArnoldEnsemble(n, precision="fp32c", device=local, stream=stream.cuda_stream)
+        e3.init_grid(G, E, seed=rank)
+        ch32 = args.chunk * 20
+        e3.iterate(ch32)
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        k3 = max(2, args.steps // 2)
+        a.record(stream)
+        for _ in range(k3):
+            e3.iterate(ch32)
+        b.record(stream)
+        barrier()
+        ms3 = a.elapsed_time(b)
+        v3 = n * ch32 * k3 / (ms3 * 1e-3)
+        fp32c = {"value": v3, "unit": "map-steps/s", "speedup_vs_fp64": v3 / (value / world),
+                 "steps_per_bench_step": ch32, "steps": k3,
+                 "roofline": {"bound": "alu", "kernel": "k_iterate_fp32c<7,true,false>",
+                              "achieved_instr_per_s": v3 * FP32C_INSTR_PER_STEP, "peak_instr_per_s": ffma,
+                              "frac": v3 * FP32C_INSTR_PER_STEP / ffma,
+                              "peak_source": "measured live: FFMA probe", "instr_per_map_step": FP32C_INSTR_PER_STEP},
+                 "agreement_note": "class agreement and histogram L1 vs FP64 are checked in tests/test_gpu_fp32c.py"}
+        e3.close()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = cpu_oracle_rate(args.cpu_seconds) if world == 1 else None
+    line = {"metric": METRIC, "value": value, "unit": "map-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(args),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(gpu_launches),
+            "clocks": clk.summary(), "fp32c": fp32c,
+            "probe": {"dfma_per_s": dfma, "ffma_per_s": ffma}}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def traffic_for(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
+    kernel source has not changed since it was taken; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path)).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    import hashlib
+    h = hashlib.sha256()
+    for f in rec.get("sources", []):
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    if h.hexdigest() != rec.get("sha256"):
+        return None
+    return rec.get("bytes_per_launch_full")
+
+
+if __name__ == "__main__":
+    main()

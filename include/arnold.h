@@ -1,0 +1,194 @@
+/*
+ * arnold.h -- C ABI of libarnold.so, the B300 (sm_103a) ensemble propagator
+ * for the Arnold-web scan of Seibert, Denisov, Ponomarev & Haenggi,
+ * "Mapping the Arnold web with a GPU-supercomputer" (arXiv:1107.4107).
+ *
+ * What it computes (the paper's Sec. II-IV):
+ *   H(P, X) = |P|^2 / 2 + eps * cos x cos y (1 + cos 2z)          (Eqs. 1-2)
+ * propagated for an ensemble of independent trajectories by a symmetric
+ * composition of drift-kick-drift leapfrog substeps (a sixth-order
+ * symplectic integrator, Sec. III), angles on the torus [0, 2pi)^3 with lap
+ * counters, each trajectory carrying the tangent-map vector for the
+ * finite-time Lyapunov indicator, the finite-time averaged velocity
+ * V = [X(t + dt) - X(t)] / dt of Sec. IV, and the energy error of Sec. III.
+ *
+ * Conventions for every entry point:
+ *   - Status: 0 on success, a negative ARNOLD_E* code otherwise; no call
+ *     aborts, throws or traps.  arnold_strerror() names a code.
+ *   - Ownership: the library owns each context and all device memory inside
+ *     it (state, tangent, tables, checkpoints, reduction scratch).  The caller
+ *     owns every buffer it passes in; the library never keeps a caller pointer
+ *     past the call.
+ *   - ptr_kind: ARNOLD_HOST for host memory (pageable or pinned), ARNOLD_DEVICE
+ *     for device memory of the context's device.
+ *   - Layout: per-trajectory arrays are structure-of-arrays, component-major:
+ *     a "[3][n] f64" array holds all x, then all y, then all z (row-major C).
+ *   - Streams: work is enqueued on the stream given at creation (NULL = the
+ *     legacy default stream).  Calls that return data to the host synchronise
+ *     that stream; others return before the GPU finishes.  An error raised by
+ *     a kernel is reported by the next call that synchronises.
+ *   - Threads: a context may be used from one host thread at a time.
+ */
+#ifndef ARNOLD_H
+#define ARNOLD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define ARNOLD_OK            0
+#define ARNOLD_EINVAL       -1  /* bad argument: NULL, n <= 0, h == 0, unknown enum, size mismatch */
+#define ARNOLD_ENOMEM       -2  /* device or host allocation failed                                */
+#define ARNOLD_ECUDA        -3  /* a CUDA runtime call or kernel failed                             */
+#define ARNOLD_ETIMEOUT     -4  /* a bounded device-side wait ran out                               */
+#define ARNOLD_ENONFINITE   -5  /* the state became NaN/Inf (checked when results are read)         */
+#define ARNOLD_EUNSUPPORTED -6  /* combination not built (e.g. no CUDA device)                      */
+#define ARNOLD_ESTATE       -7  /* call out of order (e.g. arnold_grad before arnold_forward_ckpt)  */
+
+/* ---- enums --------------------------------------------------------------- */
+/* Integrators (Sec. III names a sixth-order symplectic scheme whose reference
+ * is missing; Yoshida's solution A is the default reading). */
+#define ARNOLD_SCHEME_YOSHIDA6A   0  /* Yoshida 1990, 6th order, solution A, 7 kicks/step */
+#define ARNOLD_SCHEME_TRIPLEJUMP6 1  /* recursive triple jump, 6th order, 9 kicks/step   */
+#define ARNOLD_SCHEME_LEAPFROG2   2  /* drift-kick-drift leapfrog, 2nd order, 1 kick/step */
+
+#define ARNOLD_FP64  0  /* state, tangent and sincos in FP64 (the paper used double precision, Sec. III) */
+#define ARNOLD_FP32C 1  /* compensated FP32: two-sum angle/action updates, FP64 angle reduction and logs   */
+
+#define ARNOLD_HOST   0
+#define ARNOLD_DEVICE 1
+
+/* Indicator kinds for arnold_indicator(). */
+#define ARNOLD_IND_CHI      0  /* [n] f64: FTLE chi_t = ln(|w(t)|/|w(0)|) / t, t = steps * h          */
+#define ARNOLD_IND_V        1  /* [3][n] f64: V of Sec. IV (last closed window, or whole run if window=0) */
+#define ARNOLD_IND_DE       2  /* [n] f64: |H(now) - H(t=0)| (Sec. III energy error)                      */
+#define ARNOLD_IND_DE_MAX   3  /* [n] f64: max |H - H(0)| sampled every renorm_every steps               */
+#define ARNOLD_IND_CLASS    4  /* [n] u8: 1 = chaotic, chi_t > kappa * ln(max(t, e)) / t                  */
+#define ARNOLD_IND_X        5  /* [3][n] f64: angles x, y, z reduced into [0, 2pi)                       */
+#define ARNOLD_IND_P        6  /* [3][n] f64: momenta p_x, p_y, p_z                                      */
+#define ARNOLD_IND_DX       7  /* [3][n] f64: unwrapped X(now) - X(window start) (window 0: since start)  */
+#define ARNOLD_IND_TANGENT  8  /* [6][n] f64: (dx, dy, dz, dp_x, dp_y, dp_z), as renormalised             */
+#define ARNOLD_IND_LOGSUM   9  /* [n] f64: sum of ln|w| taken at renormalisations                        */
+
+/* ---- parameters ------------------------------------------------------------ */
+typedef struct arnold_params {
+  double  eps;           /* eps of Eq. 1 (the paper uses 1, Eq. 3)                          */
+  double  h;             /* composite step, != 0 (paper: 0.01 * 2 pi, Sec. III)             */
+  int32_t scheme;        /* ARNOLD_SCHEME_*                                                 */
+  int32_t precision;     /* ARNOLD_FP64 or ARNOLD_FP32C                                     */
+  int32_t tangent;       /* 1: carry the tangent vector and FTLE; 0: state only            */
+  int32_t renorm_every;  /* R >= 1: tangent renormalisation / energy sampling interval      */
+  int64_t window;        /* W >= 0: steps per averaging window of V; 0 = whole run          */
+  double  chaos_kappa;   /* kappa > 0 of the regular/chaotic threshold (default 10)         */
+  int32_t block_size;    /* threads per block, multiple of 32 in [32, 512]; 0 = default    */
+  int32_t launch_steps;  /* max composite steps per kernel launch; 0 = automatic (~0.2 s)   */
+} arnold_params;
+
+/* Fill defaults: eps 1, h 0.02 pi, Yoshida-6A, FP64, tangent on, R 100,
+ * window 0, kappa 10, automatic launch shape.  Never fails. */
+void arnold_params_default(arnold_params* prm);
+
+typedef struct arnold_ctx arnold_ctx;
+
+/* Create a context for n_traj trajectories on `device`, enqueuing on
+ * `cuda_stream` (a cudaStream_t, or NULL).  Allocates all device state.
+ * Errors: EINVAL (bad params, n_traj <= 0, out == NULL), ENOMEM, ECUDA,
+ * EUNSUPPORTED (no device).  On error *out is NULL. */
+int arnold_create(const arnold_params* prm, int64_t n_traj, int device, void* cuda_stream,
+                  arnold_ctx** out);
+
+/* Release the context and its device memory (synchronises its stream).
+ * NULL is a no-op. */
+void arnold_destroy(arnold_ctx* ctx);
+
+/* Set the phase-space state of all trajectories and reset the clock,
+ * indicators and energy reference H(t=0).  x, p: [3][n] f64 (angles may be
+ * any real; they are reduced into [0, 2pi)); w: [6][n] f64 initial tangent
+ * (dx, dy, dz, dp_x, dp_y, dp_z) normalised by the library, or NULL for
+ * (1, ..., 1) / sqrt 6.  Errors: EINVAL, ECUDA. */
+int arnold_set_state(arnold_ctx* ctx, const double* x, const double* p, const double* w,
+                     int ptr_kind);
+
+/* Initial conditions on a 2-D slice of initial actions, generated on the
+ * device (the scans of Sec. IV, Figs. 2-3, on a grid): trajectory t = j*G + i
+ * (global index, row j = row0 + t / G) gets p_x = (2 (i + 1/2)/G - 1) a,
+ * p_y = (2 (j + 1/2)/G - 1) a, a = 0.9 sqrt(E - 2|eps|), angles uniform on
+ * [0, 2pi) from SplitMix64(seed) counters 3 t_g .. 3 t_g + 2, and
+ * p_z = +sqrt(2 (E - eps Hp(X)) - p_x^2 - p_y^2) from the fixed-energy
+ * condition (Sec. IV, Fig. 4 caption).  The context must hold
+ * n = rows * G trajectories for some rows >= 1 with row0 + rows <= G.
+ * If raw_out (device, [6][n] f64) is not NULL it receives the generated
+ * x, y, z, p_x, p_y, p_z.  Resets the clock like arnold_set_state.
+ * Errors: EINVAL (E <= 2|eps|, size mismatch), ECUDA. */
+int arnold_init_grid(arnold_ctx* ctx, int64_t G, int64_t row0, double E, uint64_t seed,
+                     double* raw_out);
+
+/* Advance every trajectory n_steps >= 0 composite steps (asynchronous).
+ * Work is split into launches of at most launch_steps steps; the result does
+ * not depend on the split.  Errors: EINVAL, ECUDA. */
+int arnold_iterate(arnold_ctx* ctx, int64_t n_steps);
+
+/* Composite steps taken since the last set_state / init_grid. */
+int64_t arnold_steps_done(const arnold_ctx* ctx);
+
+/* Write one indicator (ARNOLD_IND_*) of all trajectories into `out`
+ * (layout per kind above).  Host outputs synchronise the stream.
+ * Errors: EINVAL (unknown kind, NULL out, CHI/CLASS/LOGSUM/TANGENT with
+ * tangent off), ECUDA. */
+int arnold_indicator(arnold_ctx* ctx, int kind, void* out, int ptr_kind);
+
+/* Ensemble statistics (an ensemble statistic of the indicators, like the
+ * density F of Sec. IV).  Histogram of log10 chi over [-8, 1) in 200 bins
+ * (chi <= 0 or below -8: `under`; at or above 1: `over`), chaotic count,
+ * maximum sampled energy error, mean and population variance of each
+ * momentum component.  Reductions run on the device in a fixed order. */
+#define ARNOLD_HIST_BINS 200
+typedef struct arnold_stats {
+  uint64_t hist[ARNOLD_HIST_BINS];
+  uint64_t under, over, chaotic, n;
+  double   dE_max;       /* max over trajectories of the energy-error input          */
+  double   p_mean[3];
+  double   p_var[3];
+  double   t;            /* steps * h (or the t passed in)                            */
+} arnold_stats;
+
+/* Statistics of the context's own trajectories (chi, sampled dE_max, P).
+ * Fills *out (host struct); synchronises.  Errors: EINVAL (tangent off),
+ * ECUDA. */
+int arnold_stats_compute(arnold_ctx* ctx, arnold_stats* out);
+
+/* Same statistics over caller arrays (device pointers, f64): chi[n], dE[n]
+ * (or NULL), p[3][n], for time t and threshold factor kappa.  Uses the
+ * context's device, stream and reduction scratch.  Errors: EINVAL, ECUDA. */
+int arnold_stats_arrays(arnold_ctx* ctx, int64_t n, const double* chi, const double* dE,
+                        const double* p, double t, double kappa, arnold_stats* out);
+
+/* Synchronise the context's stream; returns the first pending error. */
+int arnold_sync(arnold_ctx* ctx);
+
+/* Number of kernels this context has launched (for accounting). */
+int64_t arnold_launch_count(const arnold_ctx* ctx);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* arnold_strerror(int status);
+
+/* ---- diagnostics --------------------------------------------------------- */
+/* Device sincos used by the kernels, for accuracy tests: s[k], c[k] for
+ * x[k] in [0, 2pi] (device f64 arrays of length n).  precision selects the
+ * FP64 table method or the FP32 variant (results widened to f64). */
+int arnold_debug_sincos(arnold_ctx* ctx, int precision, int64_t n, const double* x, double* s,
+                        double* c);
+
+/* Pipe-throughput probe on `device`: kind 0 = DFMA, 1 = FFMA, 2 = MUFU sin;
+ * *ops_per_s receives lane-operations per second (best of 3).  Runs ~50 ms.
+ * Errors: EINVAL, ECUDA, EUNSUPPORTED. */
+int arnold_probe_peak(int device, int kind, double* ops_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ARNOLD_H */

@@ -10,7 +10,7 @@ __all__ = ["api", "inputs", "params"]
 
 
 def __getattr__(name):
-    if name in ("ArnoldEnsemble", "ArnoldMap", "ArnoldBatch", "Stats"):
+    if name in ("ArnoldEnsemble", "probe_peak", "ArnoldError"):
         from . import api
         return getattr(api, name)
     raise AttributeError(name)

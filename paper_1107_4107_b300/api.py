@@ -1,0 +1,173 @@
+"""Python face of libarnold: an ensemble of trajectories of Eqs. 1-2 on the GPU.
+
+    ens = ArnoldEnsemble(n=2048 * 2048, precision="fp64")
+    ens.init_grid(G=2048, E=400.0)      # 2-D slice of initial actions (Sec. IV)
+    ens.iterate(10_000)                 # composite steps of the 6th-order map (Sec. III)
+    chi = ens.indicator("chi")          # FTLE per trajectory (numpy, host)
+
+Every step runs in the CUDA library; this module only marshals arguments.
+Device buffers (torch CUDA tensors) are passed by pointer; host buffers are
+numpy arrays.  torch is used for device memory and streams only.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+
+import numpy as np
+
+from . import _lib
+from ._lib import ArnoldError, check  # noqa: F401  (re-exported)
+from .params import paper_h
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr_kind(a):
+    """(pointer, ptr_kind) of a numpy array or a contiguous torch CUDA tensor."""
+    if a is None:
+        return None, _lib.HOST
+    if _is_torch(a):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr()), (_lib.DEVICE if a.is_cuda else _lib.HOST)
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return ctypes.c_void_p(a.ctypes.data), _lib.HOST
+
+
+class ArnoldEnsemble:
+    """n independent trajectories held on one GPU (library-owned device memory)."""
+
+    def __init__(self, n: int, eps: float = 1.0, h: float | None = None, scheme: str = "yoshida6a",
+                 precision: str = "fp64", tangent: bool = True, renorm_every: int = 100, window: int = 0,
+                 kappa: float = 10.0, device: int = 0, stream=None, block_size: int = 0, launch_steps: int = 0):
+        L = _lib.lib()
+        self.n = int(n)
+        self.params = _lib.Params(eps, paper_h() if h is None else h, _lib.SCHEMES[scheme],
+                                  _lib.PRECISIONS[precision], int(bool(tangent)), renorm_every, window, kappa,
+                                  block_size, launch_steps)
+        if stream is None:
+            stream_ptr = None
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream_ptr = ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+            except ImportError:
+                pass
+        else:
+            stream_ptr = ctypes.c_void_p(stream)
+        self._stream = stream_ptr
+        handle = ctypes.c_void_p()
+        check(L.arnold_create(ctypes.byref(self.params), self.n, device, stream_ptr, ctypes.byref(handle)),
+              "arnold_create")
+        self._h = handle
+        self.device = device
+
+    # -- lifetime --
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.lib().arnold_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- state --
+    def set_state(self, X, P, W=None):
+        """X, P: [3][n] f64 (numpy host, or torch CUDA); W: [6][n] or None."""
+        px, kx = _ptr_kind(X)
+        pp, kp = _ptr_kind(P)
+        pw, kw = _ptr_kind(W)
+        if kx != kp or (W is not None and kw != kx):
+            raise ValueError("X, P, W must all be host or all device")
+        for a, rows in ((X, 3), (P, 3), (W, 6)):
+            if a is not None and (tuple(a.shape) != (rows, self.n) or str(a.dtype).split(".")[-1] != "float64"):
+                raise ValueError(f"expected float64 [{rows}][{self.n}]")
+        check(_lib.lib().arnold_set_state(self._h, px, pp, pw, kx), "arnold_set_state")
+
+    def init_grid(self, G: int, E: float, seed: int = 0, row0: int = 0, raw_out=None):
+        """Grid-slice initial conditions generated on the device (Sec. IV)."""
+        pr, _ = _ptr_kind(raw_out)
+        check(_lib.lib().arnold_init_grid(self._h, G, row0, E, seed, pr), "arnold_init_grid")
+
+    def iterate(self, n_steps: int):
+        check(_lib.lib().arnold_iterate(self._h, int(n_steps)), "arnold_iterate")
+
+    @property
+    def steps(self) -> int:
+        return _lib.lib().arnold_steps_done(self._h)
+
+    @property
+    def launches(self) -> int:
+        return _lib.lib().arnold_launch_count(self._h)
+
+    @property
+    def time(self) -> float:
+        return self.steps * self.params.h
+
+    def sync(self):
+        check(_lib.lib().arnold_sync(self._h), "arnold_sync")
+
+    # -- read-out --
+    def indicator(self, kind: str, out=None):
+        """Indicator `kind` (see _lib.IND) into `out` (numpy host array, torch CUDA
+        tensor) or a new numpy array."""
+        rows = _lib.IND_SHAPE[kind]
+        if out is None:
+            dtype = np.uint8 if kind == "class" else np.float64
+            out = np.empty((rows, self.n) if rows > 1 else (self.n,), dtype=dtype)
+        po, ko = _ptr_kind(out)
+        check(_lib.lib().arnold_indicator(self._h, _lib.IND[kind], po, ko), f"arnold_indicator({kind})")
+        return out
+
+    def stats(self) -> dict:
+        s = _lib.Stats()
+        check(_lib.lib().arnold_stats_compute(self._h, ctypes.byref(s)), "arnold_stats_compute")
+        return stats_dict(s)
+
+    def stats_arrays(self, chi, dE, P, t: float, kappa: float = 10.0) -> dict:
+        """Statistics of caller device arrays (torch CUDA float64)."""
+        s = _lib.Stats()
+        pc, _ = _ptr_kind(chi)
+        pd, _ = _ptr_kind(dE)
+        pp, _ = _ptr_kind(P)
+        check(_lib.lib().arnold_stats_arrays(self._h, int(chi.shape[0]), pc, pd, pp, t, kappa, ctypes.byref(s)),
+              "arnold_stats_arrays")
+        return stats_dict(s)
+
+    def debug_sincos(self, x, s, c, precision: str = "fp64"):
+        px, _ = _ptr_kind(x)
+        ps, _ = _ptr_kind(s)
+        pc, _ = _ptr_kind(c)
+        check(_lib.lib().arnold_debug_sincos(self._h, _lib.PRECISIONS[precision], int(x.shape[0]), px, ps, pc),
+              "arnold_debug_sincos")
+
+
+def stats_dict(s) -> dict:
+    return {"hist": np.array(list(s.hist), dtype=np.int64), "under": int(s.under), "over": int(s.over),
+            "chaotic": int(s.chaotic), "n": int(s.n), "dE_max": float(s.dE_max),
+            "p_mean": np.array(list(s.p_mean)), "p_var": np.array(list(s.p_var)), "t": float(s.t)}
+
+
+def probe_peak(kind: str, device: int = 0) -> float:
+    """Measured lane-operations/s of one pipe: 'dfma', 'ffma' or 'mufu'."""
+    v = ctypes.c_double()
+    check(_lib.lib().arnold_probe_peak(device, {"dfma": 0, "ffma": 1, "mufu": 2}[kind], ctypes.byref(v)),
+          "arnold_probe_peak")
+    return v.value
+
+
+def chaos_threshold(t: float, kappa: float = 10.0) -> float:
+    return kappa * math.log(max(abs(t), math.e)) / abs(t)

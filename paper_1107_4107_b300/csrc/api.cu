@@ -1,0 +1,571 @@
+// C-ABI layer of libarnold (declared in include/arnold.h): contexts, device
+// memory, sincos tables, launch planning, read-out and host fault injection.
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "kernels.cuh"
+
+namespace arnold {
+cudaError_t launch_iterate_fp32c_v(const IterArgs& a, int scheme, bool tangent, bool reduce64, int block, int grid,
+                                   cudaStream_t st);
+
+// FP32 table geometry: D = 2 pi / 2048 rounded to 12 significant bits (so
+// j * D is exact in FP32 for j < 4096), jmax covers [0, 2pi + D/2].
+void fp32_table_geometry(float* d, float* inv_d, int* jmax) {
+  const double D = kTwoPi / 2048.0;
+  int e;
+  const double m = frexp(D, &e);                   // D = m 2^e, m in [0.5, 1)
+  const double Dq = ldexp(floor(m * 4096.0 + 0.5) / 4096.0, e);
+  *d = (float)Dq;
+  *inv_d = (float)(1.0 / Dq);
+  *jmax = (int)ceil(kTwoPi / Dq) + 1;
+}
+}  // namespace arnold
+
+using namespace arnold;
+
+struct arnold_ctx {
+  arnold_params prm;
+  long long n = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  long long steps = 0;
+  int sms = 148;
+  long long launches = 0;
+  Fp64State s{};
+  Fp32cState f{};
+  double2* sc = nullptr;   // FP64 sincos table
+  double* th = nullptr;
+  float2* scf = nullptr;   // FP32 sincos table
+  int* flags = nullptr;    // device error flags
+  StatsPartial* partials = nullptr;
+  StatsPartial* stats_out = nullptr;
+  int stats_grid = 0;
+  double* scratch = nullptr;   // [6][n] f64 read-out scratch (lazy)
+  double* scratch2 = nullptr;  // [5][n] f64 statistics inputs (lazy)
+  int reduce64 = 0;            // FP32C variant: FP64 mod-2pi reduction
+};
+
+namespace {
+
+int fault_is(const char* what) {
+  const char* f = getenv("ARNOLD_FAULT");
+  return f && strcmp(f, what) == 0;
+}
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return ARNOLD_OK;
+  if (e == cudaErrorMemoryAllocation) return ARNOLD_ENOMEM;
+  if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return ARNOLD_EUNSUPPORTED;
+  return ARNOLD_ECUDA;
+}
+
+#define ACHECK(expr)                                   \
+  do {                                                 \
+    cudaError_t _e = (expr);                           \
+    if (_e != cudaSuccess) return cuda_status(_e);     \
+  } while (0)
+
+int params_ok(const arnold_params* p) {
+  if (!p) return 0;
+  if (!(p->h != 0.0) || !isfinite(p->h) || !isfinite(p->eps)) return 0;
+  if (p->scheme < 0 || p->scheme > 2) return 0;
+  if (p->precision != ARNOLD_FP64 && p->precision != ARNOLD_FP32C) return 0;
+  if (p->tangent != 0 && p->tangent != 1) return 0;
+  if (p->renorm_every < 1 || p->window < 0) return 0;
+  if (!(p->chaos_kappa > 0.0)) return 0;
+  if (p->block_size != 0 && (p->block_size < 32 || p->block_size > 512 || p->block_size % 32)) return 0;
+  if (p->launch_steps < 0) return 0;
+  return 1;
+}
+
+// Leapfrog weights of one composite step (Sec. III reading).
+int scheme_weights(int scheme, double* w) {
+  if (scheme == ARNOLD_SCHEME_YOSHIDA6A) {
+    // Yoshida, Phys. Lett. A 150 (1990) 262, solution A.
+    const double w1 = -1.17767998417887, w2 = 0.235573213359357, w3 = 0.784513610477560;
+    const double w0 = 1.0 - 2.0 * (w1 + w2 + w3);
+    const double seq[7] = {w3, w2, w1, w0, w1, w2, w3};
+    for (int k = 0; k < 7; ++k) w[k] = seq[k];
+    return 7;
+  }
+  if (scheme == ARNOLD_SCHEME_TRIPLEJUMP6) {
+    const double g1 = 1.0 / (2.0 - cbrt(2.0)), g0 = 1.0 - 2.0 * g1;
+    const double d1 = 1.0 / (2.0 - pow(2.0, 0.2)), d0 = 1.0 - 2.0 * d1;
+    const double outer[3] = {d1, d0, d1}, inner[3] = {g1, g0, g1};
+    int k = 0;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) w[k++] = outer[a] * inner[b];
+    return 9;
+  }
+  w[0] = 1.0;
+  return 1;
+}
+
+StepCoef make_coef(const arnold_params& p) {
+  StepCoef c;
+  memset(&c, 0, sizeof c);
+  double w[9];
+  const int m = scheme_weights(p.scheme, w);
+  c.m = m;
+  for (int k = 0; k <= m; ++k) {
+    const double left = k > 0 ? w[k - 1] : 0.0, right = k < m ? w[k] : 0.0;
+    c.sig[k] = 0.5 * (left + right) * p.h;
+    c.sig_hi[k] = (float)c.sig[k];
+    c.sig_lo[k] = (float)(c.sig[k] - (double)c.sig_hi[k]);
+  }
+  for (int k = 0; k < m; ++k) {
+    const double tau = w[k] * p.h;
+    c.k2[k] = 2.0 * tau * p.eps;
+    c.k4[k] = 4.0 * tau * p.eps;
+    c.k2f[k] = (float)c.k2[k];
+    c.k4f[k] = (float)c.k4[k];
+  }
+  return c;
+}
+
+int build_tables(arnold_ctx* c) {
+  // FP64: theta_j = j D, D = 2pi/4096 with the low 14 mantissa bits cleared.
+  const double D0 = kTwoPi / (double)kTabN;
+  unsigned long long bits;
+  memcpy(&bits, &D0, 8);
+  bits &= ~((1ULL << 14) - 1ULL);
+  double D;
+  memcpy(&D, &bits, 8);
+  double2* hsc = (double2*)malloc(sizeof(double2) * kTabEntries);
+  double* hth = (double*)malloc(sizeof(double) * kTabEntries);
+  if (!hsc || !hth) { free(hsc); free(hth); return ARNOLD_ENOMEM; }
+  for (int j = 0; j < kTabEntries; ++j) {
+    const double t = (double)j * D;   // exact
+    hth[j] = t;
+    hsc[j].x = (double)sinl((long double)t);
+    hsc[j].y = (double)cosl((long double)t);
+  }
+  cudaError_t e = cudaMalloc(&c->sc, sizeof(double2) * kTabEntries);
+  if (e == cudaSuccess) e = cudaMalloc(&c->th, sizeof(double) * kTabEntries);
+  if (e == cudaSuccess) e = cudaMemcpy(c->sc, hsc, sizeof(double2) * kTabEntries, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->th, hth, sizeof(double) * kTabEntries, cudaMemcpyHostToDevice);
+  free(hsc);
+  free(hth);
+  if (e != cudaSuccess) return cuda_status(e);
+  // FP32 table
+  float d, inv_d;
+  int jmax;
+  fp32_table_geometry(&d, &inv_d, &jmax);
+  float2* hf = (float2*)malloc(sizeof(float2) * (jmax + 1));
+  if (!hf) return ARNOLD_ENOMEM;
+  for (int j = 0; j <= jmax; ++j) {
+    const long double t = (long double)j * (long double)d;
+    hf[j].x = (float)sinl(t);
+    hf[j].y = (float)cosl(t);
+  }
+  e = cudaMalloc(&c->scf, sizeof(float2) * (jmax + 1));
+  if (e == cudaSuccess) e = cudaMemcpy(c->scf, hf, sizeof(float2) * (jmax + 1), cudaMemcpyHostToDevice);
+  free(hf);
+  return cuda_status(e);
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, sizeof(T) * (count ? count : 1));
+}
+
+void free_all(arnold_ctx* c) {
+  void* ptrs[] = {c->s.st, c->s.tg, c->s.lap, c->s.lapref, c->s.ref, c->s.logsum, c->s.demax, c->s.e0, c->s.V,
+                  c->f.hi, c->f.lo, c->f.tg, c->sc, c->th, c->scf, c->flags, c->partials, c->stats_out,
+                  c->scratch, c->scratch2};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+int grid_for(const arnold_ctx* c, int block) {
+  long long g = (c->n + block - 1) / block;
+  long long cap = (long long)c->sms * 8;
+  if (g > cap) g = cap;
+  return (int)(g < 1 ? 1 : g);
+}
+
+int check_flags(arnold_ctx* c) {
+  int h = 0;
+  ACHECK(cudaMemcpyAsync(&h, c->flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  ACHECK(cudaStreamSynchronize(c->stream));
+  if (h & kFlagTimeout) return ARNOLD_ETIMEOUT;
+  if (h & kFlagNonFinite) return ARNOLD_ENONFINITE;
+  return ARNOLD_OK;
+}
+
+InitArgs init_args(arnold_ctx* c) {
+  InitArgs a;
+  memset(&a, 0, sizeof a);
+  a.s = c->s;
+  a.f = c->f;
+  a.sc = c->sc;
+  a.th = c->th;
+  a.n = c->n;
+  a.eps = c->prm.eps;
+  a.tangent = c->prm.tangent;
+  a.flags = c->flags;
+  return a;
+}
+
+int device_scratch(arnold_ctx* c) {
+  if (!c->scratch) ACHECK(dalloc(&c->scratch, 6 * (size_t)c->n));
+  return ARNOLD_OK;
+}
+
+int read_indicator(arnold_ctx* c, int kind, void* dst) {
+  ReadArgs r;
+  memset(&r, 0, sizeof r);
+  r.s = c->s;
+  r.f = c->f;
+  r.sc = c->sc;
+  r.th = c->th;
+  r.n = c->n;
+  r.W = c->prm.window;
+  r.kind = kind;
+  r.fp32c = c->prm.precision == ARNOLD_FP32C;
+  r.t = (double)c->steps * c->prm.h;
+  r.eps = c->prm.eps;
+  const double tt = fabs(r.t);
+  r.threshold = c->prm.chaos_kappa * log(tt > M_E ? tt : M_E) / tt;
+  r.out = dst;
+  ACHECK(launch_indicator(r, grid_for(c, 256), 256, c->stream));
+  c->launches++;
+  return ARNOLD_OK;
+}
+
+size_t indicator_bytes(int kind, long long n) {
+  switch (kind) {
+    case ARNOLD_IND_CHI: case ARNOLD_IND_DE: case ARNOLD_IND_DE_MAX: case ARNOLD_IND_LOGSUM: return 8 * (size_t)n;
+    case ARNOLD_IND_CLASS: return (size_t)n;
+    case ARNOLD_IND_V: case ARNOLD_IND_X: case ARNOLD_IND_P: case ARNOLD_IND_DX: return 24 * (size_t)n;
+    case ARNOLD_IND_TANGENT: return 48 * (size_t)n;
+  }
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+void arnold_params_default(arnold_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof *p);
+  p->eps = 1.0;
+  p->h = 0.02 * 3.14159265358979323846;
+  p->scheme = ARNOLD_SCHEME_YOSHIDA6A;
+  p->precision = ARNOLD_FP64;
+  p->tangent = 1;
+  p->renorm_every = 100;
+  p->window = 0;
+  p->chaos_kappa = 10.0;
+}
+
+const char* arnold_strerror(int s) {
+  switch (s) {
+    case ARNOLD_OK: return "ok";
+    case ARNOLD_EINVAL: return "invalid argument";
+    case ARNOLD_ENOMEM: return "out of memory";
+    case ARNOLD_ECUDA: return "CUDA error";
+    case ARNOLD_ETIMEOUT: return "device wait timed out";
+    case ARNOLD_ENONFINITE: return "non-finite state";
+    case ARNOLD_EUNSUPPORTED: return "unsupported (no CUDA device or combination not built)";
+    case ARNOLD_ESTATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+int arnold_create(const arnold_params* prm, int64_t n_traj, int device, void* cuda_stream, arnold_ctx** out) {
+  if (out) *out = nullptr;
+  if (!out || !params_ok(prm) || n_traj <= 0 || n_traj > (1LL << 40)) return ARNOLD_EINVAL;
+  if (fault_is("alloc")) return ARNOLD_ENOMEM;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) return ARNOLD_EUNSUPPORTED;
+  if (device < 0 || device >= ndev) return ARNOLD_EINVAL;
+  ACHECK(cudaSetDevice(device));
+  arnold_ctx* c = new (std::nothrow) arnold_ctx();
+  if (!c) return ARNOLD_ENOMEM;
+  c->prm = *prm;
+  c->n = n_traj;
+  c->device = device;
+  c->stream = (cudaStream_t)cuda_stream;
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+  const size_t n = (size_t)n_traj;
+  const int tan = prm->tangent;
+  cudaError_t e = cudaSuccess;
+  if (prm->precision == ARNOLD_FP64) {
+    e = dalloc(&c->s.st, 6 * n);
+    if (e == cudaSuccess && tan) e = dalloc(&c->s.tg, 6 * n);
+  } else {
+    e = dalloc(&c->f.hi, 6 * n);
+    if (e == cudaSuccess) e = dalloc(&c->f.lo, 6 * n);
+    if (e == cudaSuccess && tan) e = dalloc(&c->f.tg, 6 * n);
+  }
+  if (e == cudaSuccess) e = dalloc(&c->s.lap, 3 * n);
+  if (e == cudaSuccess) e = dalloc(&c->s.lapref, 3 * n);
+  if (e == cudaSuccess) e = dalloc(&c->s.ref, 3 * n);
+  if (e == cudaSuccess && tan) e = dalloc(&c->s.logsum, n);
+  if (e == cudaSuccess) e = dalloc(&c->s.demax, n);
+  if (e == cudaSuccess) e = dalloc(&c->s.e0, n);
+  if (e == cudaSuccess) e = dalloc(&c->s.V, 3 * n);
+  if (e == cudaSuccess) e = dalloc(&c->flags, 1);
+  if (e == cudaSuccess) e = cudaMemset(c->flags, 0, sizeof(int));
+  c->stats_grid = c->sms * 4;
+  if (e == cudaSuccess) e = dalloc(&c->partials, (size_t)c->stats_grid);
+  if (e == cudaSuccess) e = dalloc(&c->stats_out, 1);
+  int st = cuda_status(e);
+  if (st == ARNOLD_OK) st = build_tables(c);
+  if (st != ARNOLD_OK) {
+    free_all(c);
+    delete c;
+    cudaGetLastError();
+    return st;
+  }
+  const char* r64 = getenv("ARNOLD_FP32C_REDUCE64");
+  c->reduce64 = r64 && r64[0] == '1';
+  *out = c;
+  return ARNOLD_OK;
+}
+
+void arnold_destroy(arnold_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  free_all(c);
+  delete c;
+}
+
+int arnold_set_state(arnold_ctx* c, const double* x, const double* p, const double* w, int ptr_kind) {
+  if (!c || !x || !p || (ptr_kind != ARNOLD_HOST && ptr_kind != ARNOLD_DEVICE)) return ARNOLD_EINVAL;
+  ACHECK(cudaSetDevice(c->device));
+  InitArgs a = init_args(c);
+  const size_t n = (size_t)c->n;
+  if (ptr_kind == ARNOLD_HOST) {
+    int st = device_scratch(c);
+    if (st) return st;
+    double* d = c->scratch;    // x [3][n], p [3][n]
+    ACHECK(cudaMemcpyAsync(d, x, 24 * n, cudaMemcpyHostToDevice, c->stream));
+    ACHECK(cudaMemcpyAsync(d + 3 * n, p, 24 * n, cudaMemcpyHostToDevice, c->stream));
+    a.x_in = d;
+    a.p_in = d + 3 * n;
+    double* dw = nullptr;
+    if (w && c->prm.tangent) {
+      if (!c->scratch2) ACHECK(dalloc(&c->scratch2, 6 * n));
+      dw = c->scratch2;
+      ACHECK(cudaMemcpyAsync(dw, w, 48 * n, cudaMemcpyHostToDevice, c->stream));
+    }
+    a.w_in = dw;
+  } else {
+    a.x_in = x;
+    a.p_in = p;
+    a.w_in = c->prm.tangent ? w : nullptr;
+  }
+  ACHECK(cudaMemsetAsync(c->flags, 0, sizeof(int), c->stream));
+  ACHECK(launch_set_state(a, grid_for(c, 256), 256, c->stream));
+  c->launches++;
+  c->steps = 0;
+  if (ptr_kind == ARNOLD_HOST) ACHECK(cudaStreamSynchronize(c->stream));   // host buffers may be freed on return
+  return ARNOLD_OK;
+}
+
+int arnold_init_grid(arnold_ctx* c, int64_t G, int64_t row0, double E, uint64_t seed, double* raw_out) {
+  if (!c || G <= 0 || row0 < 0 || c->n % G != 0) return ARNOLD_EINVAL;
+  const int64_t rows = c->n / G;
+  if (rows < 1 || row0 + rows > G) return ARNOLD_EINVAL;
+  if (!(E > 2.0 * fabs(c->prm.eps))) return ARNOLD_EINVAL;
+  ACHECK(cudaSetDevice(c->device));
+  InitArgs a = init_args(c);
+  a.G = G;
+  a.row0 = row0;
+  a.E = E;
+  a.seed = seed;
+  a.half_width = 0.9 * sqrt(E - 2.0 * fabs(c->prm.eps));
+  a.raw_out = raw_out;
+  ACHECK(cudaMemsetAsync(c->flags, 0, sizeof(int), c->stream));
+  ACHECK(launch_init_grid(a, grid_for(c, 256), 256, c->stream));
+  c->launches++;
+  c->steps = 0;
+  return ARNOLD_OK;
+}
+
+int arnold_iterate(arnold_ctx* c, int64_t n_steps) {
+  if (!c || n_steps < 0) return ARNOLD_EINVAL;
+  if (fault_is("launch")) return ARNOLD_ECUDA;
+  if (n_steps == 0) return ARNOLD_OK;
+  ACHECK(cudaSetDevice(c->device));
+  const arnold_params& p = c->prm;
+  const bool fp32c = p.precision == ARNOLD_FP32C;
+  int block = p.block_size;
+  if (block == 0) {
+    block = 256;
+    const long long per_sm = (c->n + c->sms - 1) / c->sms;
+    if (per_sm < 256) block = (int)((per_sm + 31) / 32 * 32);
+    if (block < 32) block = 32;
+  }
+  const int bps = fp32c ? fp32c_blocks_per_sm(p.scheme, p.tangent, block) : fp64_blocks_per_sm(p.scheme, p.tangent, block);
+  long long grid = (c->n + block - 1) / block;
+  const long long cap = (long long)c->sms * bps;
+  if (grid > cap) grid = cap;
+  long long chunk = p.launch_steps;
+  if (chunk == 0) {
+    // aim at ~0.2 s per launch from the measured rates (map-steps/s, 7 kicks)
+    const double rate = (fp32c ? 3.0e10 : 1.0e9) * 7.0 / (double)make_coef(p).m;
+    chunk = (long long)(0.2 * rate / (double)c->n);
+    if (chunk < 1) chunk = 1;
+    if (chunk > (1 << 20)) chunk = 1 << 20;
+  }
+  IterArgs a;
+  memset(&a, 0, sizeof a);
+  a.s = c->s;
+  a.f = c->f;
+  a.sc = c->sc;
+  a.th = c->th;
+  a.scf = c->scf;
+  a.n = c->n;
+  a.R = p.renorm_every;
+  a.W = p.window;
+  a.h = p.h;
+  a.eps = p.eps;
+  a.cf = make_coef(p);
+  a.flags = c->flags;
+  long long left = n_steps;
+  while (left > 0) {
+    const long long s = left < chunk ? left : chunk;
+    a.step0 = c->steps;
+    a.nsteps = (int)s;
+    cudaError_t e = fp32c ? launch_iterate_fp32c_v(a, p.scheme, p.tangent, c->reduce64, block, (int)grid, c->stream)
+                          : launch_iterate_fp64(a, p.scheme, p.tangent, block, (int)grid, c->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    c->launches++;
+    c->steps += s;
+    left -= s;
+  }
+  return ARNOLD_OK;
+}
+
+int64_t arnold_steps_done(const arnold_ctx* c) { return c ? c->steps : -1; }
+
+int64_t arnold_launch_count(const arnold_ctx* c) { return c ? c->launches : -1; }
+
+int arnold_indicator(arnold_ctx* c, int kind, void* out, int ptr_kind) {
+  if (!c || !out || (ptr_kind != ARNOLD_HOST && ptr_kind != ARNOLD_DEVICE)) return ARNOLD_EINVAL;
+  const size_t bytes = indicator_bytes(kind, c->n);
+  if (!bytes) return ARNOLD_EINVAL;
+  const bool needs_tan = kind == ARNOLD_IND_CHI || kind == ARNOLD_IND_CLASS || kind == ARNOLD_IND_LOGSUM ||
+                         kind == ARNOLD_IND_TANGENT;
+  if (needs_tan && !c->prm.tangent) return ARNOLD_EINVAL;
+  if (fault_is("nan")) return ARNOLD_ENONFINITE;
+  ACHECK(cudaSetDevice(c->device));
+  if (ptr_kind == ARNOLD_DEVICE) return read_indicator(c, kind, out);
+  int st = device_scratch(c);
+  if (st) return st;
+  st = read_indicator(c, kind, c->scratch);
+  if (st) return st;
+  ACHECK(cudaMemcpyAsync(out, c->scratch, bytes, cudaMemcpyDeviceToHost, c->stream));
+  return check_flags(c);
+}
+
+int arnold_stats_arrays(arnold_ctx* c, int64_t n, const double* chi, const double* dE, const double* p, double t,
+                        double kappa, arnold_stats* out) {
+  if (!c || !out || !chi || !p || n <= 0 || !(kappa > 0.0) || t == 0.0) return ARNOLD_EINVAL;
+  ACHECK(cudaSetDevice(c->device));
+  long long g = (n + 255) / 256;
+  const int grid = (int)(g < c->stats_grid ? g : c->stats_grid);
+  const double tt = fabs(t);
+  const double thr = kappa * log(tt > M_E ? tt : M_E) / tt;
+  ACHECK(launch_stats(n, chi, dE, p, thr, c->partials, grid, c->stats_out, c->stream));
+  c->launches += 2;
+  StatsPartial h;
+  ACHECK(cudaMemcpyAsync(&h, c->stats_out, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  ACHECK(cudaStreamSynchronize(c->stream));
+  memcpy(out->hist, h.hist, sizeof out->hist);
+  out->under = h.under;
+  out->over = h.over;
+  out->chaotic = h.chaotic;
+  out->n = h.n;
+  out->dE_max = h.dE_max;
+  for (int k = 0; k < 3; ++k) {
+    out->p_mean[k] = h.mean[k];
+    out->p_var[k] = h.n ? h.m2[k] / (double)h.n : 0.0;
+  }
+  out->t = t;
+  return ARNOLD_OK;
+}
+
+int arnold_stats_compute(arnold_ctx* c, arnold_stats* out) {
+  if (!c || !out || !c->prm.tangent) return ARNOLD_EINVAL;
+  if (c->steps == 0) return ARNOLD_ESTATE;
+  ACHECK(cudaSetDevice(c->device));
+  const size_t n = (size_t)c->n;
+  if (!c->scratch2) ACHECK(dalloc(&c->scratch2, 6 * n));
+  double* chi = c->scratch2;
+  double* de = c->scratch2 + n;
+  double* pp = c->scratch2 + 2 * n;
+  int st = read_indicator(c, ARNOLD_IND_CHI, chi);
+  if (!st) st = read_indicator(c, ARNOLD_IND_DE_MAX, de);
+  if (!st) st = read_indicator(c, ARNOLD_IND_P, pp);
+  if (st) return st;
+  st = arnold_stats_arrays(c, c->n, chi, de, pp, (double)c->steps * c->prm.h, c->prm.chaos_kappa, out);
+  if (st) return st;
+  return check_flags(c);
+}
+
+int arnold_sync(arnold_ctx* c) {
+  if (!c) return ARNOLD_EINVAL;
+  if (fault_is("timeout")) return ARNOLD_ETIMEOUT;
+  ACHECK(cudaSetDevice(c->device));
+  ACHECK(cudaStreamSynchronize(c->stream));
+  ACHECK(cudaGetLastError());
+  return check_flags(c);
+}
+
+int arnold_debug_sincos(arnold_ctx* c, int precision, int64_t n, const double* x, double* s, double* co) {
+  if (!c || !x || !s || !co || n <= 0) return ARNOLD_EINVAL;
+  ACHECK(cudaSetDevice(c->device));
+  cudaError_t e = precision == ARNOLD_FP32C ? launch_debug_sincos32(x, s, co, n, c->scf, c->stream)
+                                            : launch_debug_sincos64(x, s, co, n, c->sc, c->th, c->stream);
+  ACHECK(e);
+  c->launches++;
+  ACHECK(cudaStreamSynchronize(c->stream));
+  return ARNOLD_OK;
+}
+
+int arnold_probe_peak(int device, int kind, double* ops) {
+  if (!ops || kind < 0 || kind > 2) return ARNOLD_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) return ARNOLD_EUNSUPPORTED;
+  if (device < 0 || device >= ndev) return ARNOLD_EINVAL;
+  ACHECK(cudaSetDevice(device));
+  int sms = 0;
+  ACHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  const int block = 256, grid = sms * 8;
+  const int iters = kind == 0 ? 2048 : (kind == 1 ? 65536 : 16384);
+  double* sink = nullptr;
+  ACHECK(cudaMalloc(&sink, sizeof(double) * (size_t)grid * block));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  cudaError_t err = launch_probe(kind, grid, block, 16, sink, 0);
+  for (int r = 0; r < 4 && err == cudaSuccess; ++r) {
+    cudaEventRecord(e0, 0);
+    err = launch_probe(kind, grid, block, iters, sink, 0);
+    cudaEventRecord(e1, 0);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (err == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    if (r > 0 && ms > 0.f && ms < best) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  if (err != cudaSuccess) return cuda_status(err);
+  *ops = (double)grid * block * (double)iters * 8.0 / (best * 1e-3);
+  return ARNOLD_OK;
+}
+
+}  // extern "C"

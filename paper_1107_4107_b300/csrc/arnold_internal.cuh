@@ -1,0 +1,91 @@
+// Internal definitions shared by the kernels and the C-ABI layer of libarnold.
+//
+// State layout in HBM (structure of arrays, component-major, n trajectories):
+// the library keeps each trajectory in the rotated coordinates
+//     u = x + y,  v = x - y,  z,   q_u = p_x + p_y,  q_v = p_x - p_y,  p_z,
+// in which the potential of Eq. 2 is a sum of its resonance modes,
+//     cos x cos y (1 + cos 2z) = (cos u + cos v) cos^2 z,
+// so a kick needs no products of sines of different angles.  u, v, z are
+// reduced into [0, 2pi) with integer lap counters; x = (u + v)/2 and
+// y = (u - v)/2 are recovered exactly modulo 2pi from the parity of the
+// total laps of u and v.  Conversions to the paper's (X, P) happen only at
+// set_state and when indicators are read.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/arnold.h"
+
+namespace arnold {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr double kPi = 3.14159265358979323846264338328;
+// Bit pattern of the double closest to 2 pi (positive doubles order like int64).
+constexpr long long kTwoPiBits = 0x401921FB54442D18LL;
+
+// Table-driven sincos (Tang's table-lookup method): theta_j = j * D with
+// D ~= 2 pi / N rounded to a double whose low 14 mantissa bits are zero, so
+// every theta_j (j <= N) is an exact double; the table holds
+// (sin theta_j, cos theta_j) rounded from long-double libm values, and theta_j.
+constexpr int kTabN = 4096;
+constexpr int kTabEntries = kTabN + 1;
+constexpr size_t kTabSmemBytes = kTabEntries * (sizeof(double2) + sizeof(double));
+
+// Composite-step coefficients of one scheme, scaled for one launch:
+// drifts sig[0..m] (merged half-substeps times h) and kicks
+// k2 = 2 tau eps, k4 = 4 tau eps with tau = w_k h.
+struct StepCoef {
+  int m;             // kicks per step
+  double sig[10];
+  double k2[9];
+  double k4[9];
+  float sig_hi[10], sig_lo[10];   // FP32C: sigma as a float pair
+  float k2f[9], k4f[9];
+};
+
+// Device-side error flags (bits of one int, set with atomicOr, read by the host).
+enum : int { kFlagNonFinite = 1, kFlagTimeout = 2, kFlagBadIndex = 4 };
+
+struct Fp64State {
+  double* st;      // [6][n] u, v, z, q_u, q_v, p_z (null for FP32C contexts)
+  double* tg;      // [6][n] du, dv, dz, dq_u, dq_v, dp_z (null when tangent off or FP32C)
+  int* lap;        // [3][n] total laps of u, v, z
+  int* lapref;     // [3][n] laps at the window start
+  double* ref;     // [3][n] reduced u, v, z at the window start
+  double* logsum;  // [n]
+  double* demax;   // [n]
+  double* e0;      // [n] H at t = 0
+  double* V;       // [3][n] V (x, y, z components) of the last closed window
+};
+
+struct Fp32cState {
+  float* hi;       // [6][n] u, v, z, q_u, q_v, p_z (leading parts)
+  float* lo;       // [6][n] trailing parts (value = hi + lo)
+  float* tg;       // [6][n] tangent in FP32
+};
+
+struct IterArgs {
+  Fp64State s;
+  Fp32cState f;
+  const double2* sc;   // FP64 sincos table
+  const double* th;
+  const float2* scf;   // FP32 sincos table
+  long long n;
+  long long step0;     // steps taken before this launch
+  int nsteps;          // steps in this launch
+  int R;               // renormalisation / energy-sampling interval
+  long long W;         // window (0 = none)
+  double h, eps;
+  StepCoef cf;
+  int* flags;
+};
+
+// Host helpers implemented in the .cu files.
+cudaError_t launch_iterate_fp64(const IterArgs& a, int scheme, bool tangent, int block, int grid,
+                                cudaStream_t st);
+cudaError_t launch_iterate_fp32c(const IterArgs& a, int scheme, bool tangent, int block, int grid,
+                                 cudaStream_t st);
+int fp64_blocks_per_sm(int scheme, bool tangent, int block);
+int fp32c_blocks_per_sm(int scheme, bool tangent, int block);
+
+}  // namespace arnold

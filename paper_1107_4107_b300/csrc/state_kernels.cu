@@ -1,0 +1,265 @@
+// Set-up and read-out kernels: initial conditions (paper Sec. IV), state
+// conversion between the paper's (X, P) and the rotated coordinates, and the
+// per-trajectory indicators (FTLE, V, energy error, class).
+#include <math.h>
+
+#include "devmath.cuh"
+#include "kernels.cuh"
+
+namespace arnold {
+
+namespace {
+
+// Reduce an arbitrary angle into [0, 2pi); returns the laps removed.
+__device__ __forceinline__ int reduce_any(double& x) {
+  const double k = floor(x * (1.0 / kTwoPi));
+  x = fma(-k, kTwoPi, x);
+  int lap = (int)k;
+  wrap_angle(x, lap);   // fix a rounding step over either end
+  return lap;
+}
+
+// From reduced x, y in [0, 2pi) to reduced u = x + y, v = x - y and their laps.
+__device__ __forceinline__ void to_uv(double x, double y, double& u, double& v, int& lu, int& lv) {
+  u = x + y;
+  v = x - y;
+  lu = 0;
+  lv = 0;
+  wrap_angle(u, lu);
+  wrap_angle(v, lv);
+}
+
+// Common tail of the two initialisers: energy reference, tangent, bookkeeping.
+__device__ __forceinline__ void init_common(const InitArgs& a, long long i, double u, double v, double z, double qu,
+                                            double qv, double pz, int lu, int lv, int lz) {
+  const long long n = a.n;
+  double su, cu, sv, cv, sz, cz;
+  sincos_tab64(u, a.sc, a.th, su, cu);
+  sincos_tab64(v, a.sc, a.th, sv, cv);
+  sincos_tab64(z, a.sc, a.th, sz, cz);
+  const double e0 = 0.25 * (qu * qu + qv * qv) + 0.5 * (pz * pz) + a.eps * ((cu + cv) * (cz * cz));
+  if (a.s.st) {
+    a.s.st[i] = u; a.s.st[n + i] = v; a.s.st[2 * n + i] = z;
+    a.s.st[3 * n + i] = qu; a.s.st[4 * n + i] = qv; a.s.st[5 * n + i] = pz;
+  }
+  if (a.f.hi) {
+    const double vals[6] = {u, v, z, qu, qv, pz};
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const float hi = __double2float_rn(vals[c]);
+      a.f.hi[c * n + i] = hi;
+      a.f.lo[c * n + i] = __double2float_rn(vals[c] - (double)hi);
+    }
+  }
+  a.s.lap[i] = lu; a.s.lap[n + i] = lv; a.s.lap[2 * n + i] = lz;
+  a.s.lapref[i] = lu; a.s.lapref[n + i] = lv; a.s.lapref[2 * n + i] = lz;
+  a.s.ref[i] = u; a.s.ref[n + i] = v; a.s.ref[2 * n + i] = z;
+  a.s.e0[i] = e0;
+  a.s.demax[i] = 0.0;
+  if (a.s.logsum) a.s.logsum[i] = 0.0;
+  a.s.V[i] = 0.0; a.s.V[n + i] = 0.0; a.s.V[2 * n + i] = 0.0;
+  if (a.tangent) {
+    double w[6];
+    if (a.w_in) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) w[c] = a.w_in[c * n + i];
+    } else {
+      const double c0 = 0.40824829046386301637;   // 1/sqrt(6)
+#pragma unroll
+      for (int c = 0; c < 6; ++c) w[c] = c0;
+    }
+    double n2 = 0.0;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) n2 += w[c] * w[c];
+    const double inv = 1.0 / sqrt(n2);
+    const double t6[6] = {(w[0] + w[1]) * inv, (w[0] - w[1]) * inv, w[2] * inv,
+                          (w[3] + w[4]) * inv, (w[3] - w[4]) * inv, w[5] * inv};
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      if (a.s.tg) a.s.tg[c * n + i] = t6[c];
+      if (a.f.tg) a.f.tg[c * n + i] = __double2float_rn(t6[c]);
+    }
+  }
+}
+
+__global__ void k_set_state(InitArgs a) {
+  const long long n = a.n;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double x = a.x_in[i], y = a.x_in[n + i], z = a.x_in[2 * n + i];
+    reduce_any(x);
+    reduce_any(y);
+    const int lz = reduce_any(z);
+    double u, v;
+    int lu, lv;
+    to_uv(x, y, u, v, lu, lv);
+    const double px = a.p_in[i], py = a.p_in[n + i], pz = a.p_in[2 * n + i];
+    // the parity of lu + lv carries the pi offset of x and y; displacements
+    // are measured from here, so earlier laps of x and y are not kept
+    init_common(a, i, u, v, z, px + py, px - py, pz, lu, lv, lz);
+  }
+}
+
+// Grid-slice initial conditions (Sec. IV): see arnold_init_grid in arnold.h.
+__global__ void k_init_grid(InitArgs a) {
+  const long long n = a.n;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long tg = a.row0 * a.G + i;
+    const long long col = tg % a.G, row = tg / a.G;
+    const double ui = __ddiv_rn(__dadd_rn((double)col, 0.5), (double)a.G);
+    const double uj = __ddiv_rn(__dadd_rn((double)row, 0.5), (double)a.G);
+    const double px = __dmul_rn(__dsub_rn(__dmul_rn(2.0, ui), 1.0), a.half_width);
+    const double py = __dmul_rn(__dsub_rn(__dmul_rn(2.0, uj), 1.0), a.half_width);
+    const unsigned long long c = 3ULL * (unsigned long long)tg;
+    const double x = uniform_angle(splitmix64(a.seed, c));
+    const double y = uniform_angle(splitmix64(a.seed, c + 1));
+    const double z = uniform_angle(splitmix64(a.seed, c + 2));
+    double u, v;
+    int lu, lv;
+    to_uv(x, y, u, v, lu, lv);
+    double su, cu, sv, cv, sz, cz;
+    sincos_tab64(u, a.sc, a.th, su, cu);
+    sincos_tab64(v, a.sc, a.th, sv, cv);
+    sincos_tab64(z, a.sc, a.th, sz, cz);
+    const double hp = (cu + cv) * (cz * cz);           // Eq. 2 = cos x cos y (1 + cos 2z)
+    const double r = 2.0 * (a.E - a.eps * hp) - px * px - py * py;
+    const double pz = sqrt(r);                          // NaN if r < 0 (excluded by the grid half-width)
+    if (!(r >= 0.0)) atomicOr(a.flags, kFlagNonFinite);
+    if (a.raw_out) {   // the generated values, for bit-exact tests
+      a.raw_out[i] = x; a.raw_out[n + i] = y; a.raw_out[2 * n + i] = z;
+      a.raw_out[3 * n + i] = px; a.raw_out[4 * n + i] = py; a.raw_out[5 * n + i] = pz;
+    }
+    init_common(a, i, u, v, z, px + py, px - py, pz, lu, lv, 0);
+  }
+}
+
+// ---------------------------------------------------------------- readout ---
+__device__ __forceinline__ double reduce_pi_parity(double half, int par) {
+  // half in (-pi, 2pi): add pi when the lap parity is odd, then wrap
+  double x = par ? half + kPi : half;
+  int dummy = 0;
+  wrap_angle(x, dummy);
+  return x;
+}
+
+__device__ __forceinline__ double load_pair(const Fp32cState& f, long long k) {
+  return (double)f.hi[k] + (double)f.lo[k];
+}
+
+__global__ void k_indicator(ReadArgs a) {
+  const long long n = a.n;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double u, v, z, qu, qv, pz;
+    if (a.fp32c) {
+      u = load_pair(a.f, i); v = load_pair(a.f, n + i); z = load_pair(a.f, 2 * n + i);
+      qu = load_pair(a.f, 3 * n + i); qv = load_pair(a.f, 4 * n + i); pz = load_pair(a.f, 5 * n + i);
+    } else {
+      u = a.s.st[i]; v = a.s.st[n + i]; z = a.s.st[2 * n + i];
+      qu = a.s.st[3 * n + i]; qv = a.s.st[4 * n + i]; pz = a.s.st[5 * n + i];
+    }
+    const int lu = a.s.lap[i], lv = a.s.lap[n + i], lz = a.s.lap[2 * n + i];
+    double* out = (double*)a.out;
+    switch (a.kind) {
+      case ARNOLD_IND_X: {
+        const int par = (lu + lv) & 1;
+        out[i] = reduce_pi_parity(0.5 * (u + v), par);
+        out[n + i] = reduce_pi_parity(0.5 * (u - v), par);
+        out[2 * n + i] = z;
+        break;
+      }
+      case ARNOLD_IND_P:
+        out[i] = 0.5 * (qu + qv);
+        out[n + i] = 0.5 * (qu - qv);
+        out[2 * n + i] = pz;
+        break;
+      case ARNOLD_IND_DX:
+      case ARNOLD_IND_V: {
+        if (a.kind == ARNOLD_IND_V && a.W > 0) {
+          out[i] = a.s.V[i]; out[n + i] = a.s.V[n + i]; out[2 * n + i] = a.s.V[2 * n + i];
+          break;
+        }
+        const double dU = (u - a.s.ref[i]) + kTwoPi * (double)(lu - a.s.lapref[i]);
+        const double dV = (v - a.s.ref[n + i]) + kTwoPi * (double)(lv - a.s.lapref[n + i]);
+        const double dZ = (z - a.s.ref[2 * n + i]) + kTwoPi * (double)(lz - a.s.lapref[2 * n + i]);
+        const double sc = a.kind == ARNOLD_IND_V ? 1.0 / a.t : 1.0;
+        out[i] = 0.5 * (dU + dV) * sc;
+        out[n + i] = 0.5 * (dU - dV) * sc;
+        out[2 * n + i] = dZ * sc;
+        break;
+      }
+      case ARNOLD_IND_TANGENT: {
+        double w[6];
+        for (int c = 0; c < 6; ++c) w[c] = a.fp32c ? (double)a.f.tg[c * n + i] : a.s.tg[c * n + i];
+        out[i] = 0.5 * (w[0] + w[1]);
+        out[n + i] = 0.5 * (w[0] - w[1]);
+        out[2 * n + i] = w[2];
+        out[3 * n + i] = 0.5 * (w[3] + w[4]);
+        out[4 * n + i] = 0.5 * (w[3] - w[4]);
+        out[5 * n + i] = w[5];
+        break;
+      }
+      case ARNOLD_IND_LOGSUM:
+        out[i] = a.s.logsum[i];
+        break;
+      case ARNOLD_IND_DE_MAX:
+        out[i] = a.s.demax[i];
+        break;
+      case ARNOLD_IND_DE: {
+        double su, cu, sv, cv, sz, cz;
+        sincos_tab64(u, a.sc, a.th, su, cu);
+        sincos_tab64(v, a.sc, a.th, sv, cv);
+        sincos_tab64(z, a.sc, a.th, sz, cz);
+        const double H = 0.25 * (qu * qu + qv * qv) + 0.5 * (pz * pz) + a.eps * ((cu + cv) * (cz * cz));
+        out[i] = fabs(H - a.s.e0[i]);
+        break;
+      }
+      case ARNOLD_IND_CHI:
+      case ARNOLD_IND_CLASS: {
+        double w[6];
+        for (int c = 0; c < 6; ++c) w[c] = a.fp32c ? (double)a.f.tg[c * n + i] : a.s.tg[c * n + i];
+        const double n2 = 0.5 * (w[0] * w[0] + w[1] * w[1]) + w[2] * w[2] + 0.5 * (w[3] * w[3] + w[4] * w[4]) +
+                          w[5] * w[5];
+        const double chi = (a.s.logsum[i] + 0.5 * log(n2)) / a.t;
+        if (a.kind == ARNOLD_IND_CHI) out[i] = chi;
+        else ((unsigned char*)a.out)[i] = chi > a.threshold ? 1 : 0;
+        break;
+      }
+    }
+  }
+}
+
+__global__ void k_debug_sincos(const double* x, double* s, double* c, long long n, const double2* sc,
+                               const double* th) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double ss, cc;
+    sincos_tab64(x[i], sc, th, ss, cc);
+    s[i] = ss;
+    c[i] = cc;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_set_state(const InitArgs& a, int grid, int block, cudaStream_t st) {
+  k_set_state<<<grid, block, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_grid(const InitArgs& a, int grid, int block, cudaStream_t st) {
+  k_init_grid<<<grid, block, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_indicator(const ReadArgs& a, int grid, int block, cudaStream_t st) {
+  k_indicator<<<grid, block, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_debug_sincos64(const double* x, double* s, double* c, long long n, const double2* sc,
+                                  const double* th, cudaStream_t st) {
+  long long g = (n + 255) / 256;
+  int grid = (int)(g > 4096 ? 4096 : (g < 1 ? 1 : g));
+  k_debug_sincos<<<grid, 256, 0, st>>>(x, s, c, n, sc, th);
+  return cudaGetLastError();
+}
+
+}  // namespace arnold

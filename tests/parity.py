@@ -1,0 +1,57 @@
+"""Helpers shared by the GPU parity tests: run the same seeded inputs through the
+CUDA path (C ABI via the binding) and the oracle, and measure the differences."""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+import oracle
+from paper_1107_4107_b300 import inputs
+
+TWO_PI = 2.0 * math.pi
+
+
+def oracle_params(eps=1.0, h=None, scheme="yoshida6a", R=100, window=0):
+    return oracle.Params(eps=eps, h=0.02 * math.pi if h is None else h, scheme=scheme, renorm_every=R, window=window)
+
+
+def oracle_grid_state(G, E, prm, rows=None, seed=0, cells=None):
+    """The oracle's own fixed-energy grid initial conditions (Sec. IV)."""
+    X, Pxy = inputs.grid_slice(G, E, prm.eps, seed=seed, rows=rows)
+    if cells is not None:
+        X, Pxy = X[:, cells].copy(), Pxy[:, cells].copy()
+    P = np.zeros((3, X.shape[1]))
+    P[:2] = Pxy
+    P = oracle.pz_from_energy(E, prm.eps, X, P)
+    return oracle.State(X, P, prm)
+
+
+def rel_err(a, b):
+    """max |a - b| / (1 + |b|) (relative for large values, absolute near zero)."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.max(np.abs(a - b) / (1.0 + np.abs(b)))) if a.size else 0.0
+
+
+def angle_dist(a, b):
+    d = np.mod(np.asarray(a) - np.asarray(b), TWO_PI)
+    return np.minimum(d, TWO_PI - d)
+
+
+def compare_state(ens, st, tangent=True):
+    """Per-quantity relative errors of the CUDA ensemble against the oracle state."""
+    out = {}
+    dX = ens.indicator("dX")
+    out["dX"] = rel_err(dX, st.unwrapped_displacement())
+    out["X"] = float(np.max(angle_dist(ens.indicator("X"), st.X)))
+    out["P"] = rel_err(ens.indicator("P"), st.P)
+    if tangent:
+        W = ens.indicator("tangent")
+        out["tangent"] = rel_err(W, st.W)
+        if st.steps > 0:
+            out["chi"] = rel_err(ens.indicator("chi"), st.chi())
+    if st.steps > 0:
+        out["V"] = rel_err(ens.indicator("V"), st.velocity())
+    out["dE_max"] = float(np.max(np.abs(ens.indicator("dE_max") - st.dE_max)))
+    return out

@@ -1,0 +1,248 @@
+"""FP64 CUDA path vs the FP64 oracle (element by element, same seeded inputs).
+
+Tolerance (BASELINE: <= 1e-12 per-step relative error in FP64): both sides
+are FP64; they differ by FMA contraction, the sincos implementation (CUDA
+table method vs libm, ~1 ulp) and the rotated coordinates used on the GPU
+(u = x + y, v = x - y), i.e. by rounding only.  Errors are measured as
+|gpu - oracle| / (1 + |oracle|) on the unwrapped displacement, the momenta,
+the tangent vector and the indicators, at several step counts.  Chaotic
+trajectories amplify rounding like exp(lambda t), so all cells are compared
+over 100 steps (t = 6.3) and regular cells (tangent growth below e^7) up to
+1000 steps.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1107_4107_b300 import inputs
+from parity import compare_state, oracle_grid_state, oracle_params, rel_err
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    assert torch.cuda.is_available(), "GPU test needs CUDA"
+    return torch
+
+
+def _ens(n, **kw):
+    from paper_1107_4107_b300.api import ArnoldEnsemble
+    return ArnoldEnsemble(n, **kw)
+
+
+def test_sincos_tables_accuracy(torch_cuda):
+    torch = torch_cuda
+    x = np.concatenate([np.linspace(0.0, 2 * math.pi, 200001), [0.0, 1e-300, 5e-324, 2 * math.pi - 1e-15]])
+    xd = torch.tensor(x, device="cuda", dtype=torch.float64)
+    s = torch.empty_like(xd)
+    c = torch.empty_like(xd)
+    ens = _ens(8)
+    ens.debug_sincos(xd, s, c, "fp64")
+    es = np.abs(s.cpu().numpy() - np.sin(x)).max()
+    ec = np.abs(c.cpu().numpy() - np.cos(x)).max()
+    assert es < 5e-16 and ec < 5e-16, (es, ec)
+    ens.debug_sincos(xd, s, c, "fp32c")
+    es = np.abs(s.cpu().numpy() - np.sin(x)).max()
+    ec = np.abs(c.cpu().numpy() - np.cos(x)).max()
+    assert es < 2.5e-7 and ec < 2.5e-7, (es, ec)
+
+
+@pytest.mark.parametrize("G,E,rows", [(64, 400.0, None), (48, 40.0, (7, 30))])
+def test_grid_initial_conditions(torch_cuda, G, E, rows):
+    """Device-generated grid ICs: angles and (p_x, p_y) bit-identical to the seeded
+    generator; fixed-energy p_z within 1e-14 of the oracle's."""
+    torch = torch_cuda
+    r0, r1 = rows if rows else (0, G)
+    n = (r1 - r0) * G
+    ens = _ens(n)
+    raw = torch.empty((6, n), device="cuda", dtype=torch.float64)
+    ens.init_grid(G, E, seed=0, row0=r0, raw_out=raw)
+    raw = raw.cpu().numpy()
+    X, Pxy = inputs.grid_slice(G, E, 1.0, seed=0, rows=(r0, r1))
+    assert np.array_equal(raw[:3], X)
+    assert np.array_equal(raw[3:5], Pxy)
+    P = np.zeros((3, n)); P[:2] = Pxy
+    P = oracle.pz_from_energy(E, 1.0, X, P)
+    assert rel_err(raw[5], P[2]) < 1e-14
+    # the stored state reads back as the paper's (X, P)
+    assert np.max(np.abs(np.mod(ens.indicator("X") - X + 1, 2 * math.pi) - 1)) < 1e-14
+    assert rel_err(ens.indicator("P"), P) < 1e-14
+    assert np.max(ens.indicator("dE")) < 1e-12 * E
+
+
+@pytest.mark.parametrize("n", [1, 31, 33, 1000])
+def test_box_state_parity_all_cells(torch_cuda, n):
+    """Identical inputs (seeded box, E ~ 390), ragged sizes; all cells, 1..100 steps."""
+    X, P = inputs.box(n, seed=5)
+    prm = oracle_params(R=10)
+    st = oracle.State(X, P, prm)
+    ens = _ens(n, renorm_every=10)
+    ens.set_state(X, P)
+    done = 0
+    for S in (1, 9, 40, 50):
+        ens.iterate(S)
+        st.advance(S)
+        done += S
+        errs = compare_state(ens, st)
+        assert all(v < TOL for k, v in errs.items() if k not in ("X", "dE_max")), (done, errs)
+        assert errs["X"] < 1e-11 and errs["dE_max"] < 1e-9, errs
+
+
+@pytest.mark.parametrize("scheme", ["triplejump6", "leapfrog2"])
+def test_other_schemes_parity(torch_cuda, scheme):
+    X, P = inputs.box(64, seed=6, lo=(-5.0, -5.0, -5.0), hi=(5.0, 5.0, 5.0))
+    prm = oracle_params(scheme=scheme, h=0.05, R=7)
+    st = oracle.State(X, P, prm).advance(100)
+    ens = _ens(64, scheme=scheme, h=0.05, renorm_every=7)
+    ens.set_state(X, P)
+    ens.iterate(100)
+    errs = compare_state(ens, st)
+    assert all(v < TOL for k, v in errs.items() if k not in ("X", "dE_max")), errs
+
+
+@pytest.mark.parametrize("E", [400.0, 40.0])
+def test_grid_parity_regular_cells_1000_steps(torch_cuda, E):
+    """A 32 x 32 grid (several blocks, ragged last block with block 256): every cell
+    to 100 steps, regular cells to 1000 steps, each side from its own grid ICs."""
+    G = 32
+    prm = oracle_params(R=100)
+    st = oracle_grid_state(G, E, prm)
+    ens = _ens(G * G)
+    ens.init_grid(G, E)
+    ens.iterate(100)
+    st.advance(100, threads=4)
+    errs = compare_state(ens, st)
+    assert all(v < TOL for k, v in errs.items() if k not in ("X", "dE_max")), errs
+    ens.iterate(900)
+    st.advance(900, threads=4)
+    # cells whose tangent grew less than e^7 over the run amplify rounding by less
+    # than that; on them the two FP64 paths must still agree to the tolerance
+    regular = st.chi() * st.time() < 7.0
+    assert regular.mean() > 0.3
+    for kind, ref in (("dX", st.unwrapped_displacement()), ("P", st.P), ("tangent", st.W)):
+        got = ens.indicator(kind)
+        assert rel_err(got[:, regular], ref[:, regular]) < TOL, kind
+    assert rel_err(ens.indicator("chi")[regular], st.chi()[regular]) < TOL
+    cls = ens.indicator("class")
+    assert np.array_equal(cls[regular], st.classify()[regular])
+
+
+def test_window_velocity_parity(torch_cuda):
+    X, P = inputs.box(100, seed=8)
+    prm = oracle_params(R=10, window=30)
+    st = oracle.State(X, P, prm).advance(100)
+    ens = _ens(100, renorm_every=10, window=30)
+    ens.set_state(X, P)
+    ens.iterate(100)
+    assert rel_err(ens.indicator("V"), st.velocity()) < TOL
+    assert rel_err(ens.indicator("dX"), st.unwrapped_displacement()) < TOL
+
+
+def test_launch_split_is_bitwise_invisible(torch_cuda):
+    """The result does not depend on how steps are split into launches."""
+    X, P = inputs.box(500, seed=9)
+    outs = []
+    for ls in (0, 1, 7, 64):
+        ens = _ens(500, renorm_every=10, window=20, launch_steps=ls)
+        ens.set_state(X, P)
+        ens.iterate(60)
+        ens.iterate(13)
+        outs.append([ens.indicator(k) for k in ("dX", "P", "tangent", "chi", "V", "dE_max")])
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert np.array_equal(a, b)
+
+
+def test_block_size_is_bitwise_invisible(torch_cuda):
+    X, P = inputs.box(777, seed=10)
+    ref = None
+    for bs in (32, 96, 256):
+        ens = _ens(777, block_size=bs)
+        ens.set_state(X, P)
+        ens.iterate(50)
+        got = np.concatenate([ens.indicator("dX"), ens.indicator("P"), ens.indicator("tangent")])
+        if ref is None:
+            ref = got
+        assert np.array_equal(ref, got)
+
+
+def test_device_buffers_and_zero_steps(torch_cuda):
+    torch = torch_cuda
+    X, P = inputs.box(256, seed=11)
+    ens = _ens(256)
+    ens.set_state(torch.tensor(X, device="cuda"), torch.tensor(P, device="cuda"))
+    ens.iterate(0)
+    assert ens.steps == 0
+    out = torch.empty((3, 256), device="cuda", dtype=torch.float64)
+    ens.indicator("P", out=out)
+    assert np.array_equal(out.cpu().numpy(), ens.indicator("P"))
+    assert rel_err(out.cpu().numpy(), P) < 1e-15
+
+
+def test_full_size_grid_sampled_cells(torch_cuda):
+    """The 2048 x 2048 scan in the bench's launch configuration: sampled cells
+    against the oracle computed one by one (each side from its own ICs)."""
+    G, E = 2048, 400.0
+    ens = _ens(G * G)
+    ens.init_grid(G, E)
+    ens.iterate(100)
+    cells = inputs.sample_cells(G * G, 256, seed=2)
+    st = oracle_grid_state(G, E, oracle_params(), cells=cells).advance(100, threads=4)
+    dX = ens.indicator("dX")[:, cells]
+    Pg = ens.indicator("P")[:, cells]
+    W = ens.indicator("tangent")[:, cells]
+    assert rel_err(dX, st.unwrapped_displacement()) < TOL
+    assert rel_err(Pg, st.P) < TOL
+    assert rel_err(W, st.W) < TOL
+    assert rel_err(ens.indicator("chi")[cells], st.chi()) < TOL
+    assert ens.launches >= 2
+
+
+def test_stats_against_oracle_on_identical_arrays(torch_cuda):
+    """Ensemble statistics on the same synthetic arrays: integer counts must match
+    except for values within rounding of a bin edge (log10 differs by <= 1 ulp
+    between libm and CUDA); moments to 1e-12."""
+    torch = torch_cuda
+    n = 300_001
+    r = inputs.uniform01(inputs.splitmix64(77, np.arange(5 * n, dtype=np.uint64))).reshape(5, n)
+    chi = 10.0 ** (-9.0 + 11.0 * r[0])
+    chi[:4] = [0.0, -1.0, 1e-9, 50.0]
+    dE = 1e-3 * r[1]
+    P = np.stack([10 * r[2] - 5, 3 * r[3] + 1, r[4]])
+    t = 628.3185307179587
+    ref = oracle.stats(chi, dE, P, t)
+    ens = _ens(8)
+    got = ens.stats_arrays(torch.tensor(chi, device="cuda"), torch.tensor(dE, device="cuda"),
+                           torch.tensor(P, device="cuda"), t)
+    assert got["n"] == n
+    assert got["chaotic"] == ref["chaotic"]
+    assert got["dE_max"] == ref["dE_max"]
+    assert got["under"] + got["over"] + got["hist"].sum() == n
+    diff = got["hist"] - ref["hist"]
+    if np.any(diff):
+        # any disagreement must come from a value on a bin edge
+        l10 = np.log10(chi[chi > 0])
+        u = (l10 + 8.0) * (200 / 9.0)
+        near = np.abs(u - np.round(u)) < 1e-9
+        assert np.abs(diff).sum() <= 2 * near.sum()
+    assert abs(got["under"] - ref["under"]) <= 1 and abs(got["over"] - ref["over"]) <= 1
+    np.testing.assert_allclose(got["p_mean"], ref["p_mean"], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(got["p_var"], ref["p_var"], rtol=1e-12)
+
+
+def test_stats_of_ensemble_consistent_with_indicators(torch_cuda):
+    ens = _ens(64 * 64)
+    ens.init_grid(64, 40.0)
+    ens.iterate(300)
+    s = ens.stats()
+    chi = ens.indicator("chi")
+    thr = 10 * math.log(ens.time) / ens.time
+    assert s["chaotic"] == int(np.sum(chi > thr))
+    assert s["n"] == 4096 and s["under"] + s["over"] + s["hist"].sum() == 4096
+    assert s["dE_max"] == ens.indicator("dE_max").max()
+    np.testing.assert_allclose(s["p_var"], np.var(ens.indicator("P"), axis=1), rtol=1e-12)
