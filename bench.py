@@ -130,9 +130,9 @@ def cpu_oracle_rate(seconds: float, cells: int = 512):
     P = oracle.pz_from_energy(E, EPS, X, P)
     st = oracle.State(X, P, oracle.Params(eps=EPS, h=H, renorm_every=100))
     t0 = time.perf_counter()
-    st.advance(20, threads=cores)
+    st.advance(200, threads=cores)
     dt = time.perf_counter() - t0
-    steps = max(20, int(seconds / max(dt, 1e-6) * 20))
+    steps = max(200, int(seconds / max(dt, 1e-6) * 200))
     t0 = time.perf_counter()
     st.advance(steps, threads=cores)
     dt = time.perf_counter() - t0

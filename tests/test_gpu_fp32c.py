@@ -2,10 +2,13 @@
 
 FP32C changes the arithmetic (float pairs with TwoSum/TwoProd for angles and
 momenta, FP32 forces and tangent), so pointwise agreement is bounded by the
-force rounding (~6e-8 relative per kick), not by FP64 rounding.  Stated
-bounds, |gpu - oracle| / (1 + |oracle|), regular and chaotic cells alike up
-to 100 steps, low-growth cells to 1000 steps:
-    1 step: 1e-8     100 steps: 1e-6     1000 steps (low growth): 1e-5
+force rounding, not by FP64 rounding: the FP32 table sincos is accurate to
+~9e-8 absolute, a kick changes q by at most 2 tau eps ~ 0.17, so each of the
+7 kicks of a step adds ~1.5e-8 to the momentum error (abs. ~7e-8 per step
+on |P| ~ 28, relative ~2.5e-9 ... 1.2e-8 with the 1 + |P| normalisation of
+the smaller components).  Stated bounds on |gpu - oracle| / (1 + |oracle|),
+all cells up to 100 steps, low-growth cells (tangent growth < e^5) to 1000:
+    1 step: 3e-8     100 steps: 3e-7     1000 steps (low growth): 3e-6
 Statistics: the regular/chaotic classes agree on >= 99.5 % of cells and the
 histograms of log10 chi differ by <= 1e-2 in L1 (the scan-level tolerances).
 """
@@ -20,7 +23,7 @@ from parity import oracle_grid_state, oracle_params, rel_err
 
 pytestmark = pytest.mark.gpu
 
-BOUNDS = {1: 1e-8, 100: 1e-6}
+BOUNDS = {1: 3e-8, 100: 3e-7}
 
 
 def _ens(n, **kw):
@@ -47,10 +50,10 @@ def test_fp32c_per_step_error_vs_fp64_oracle():
             report[done] = e
             assert e < BOUNDS[done], (done, e)
         else:
-            low = st.chi() * st.time() < 7.0
+            low = st.chi() * st.time() < 5.0
             e = max(rel_err(dX[:, low], st.unwrapped_displacement()[:, low]), rel_err(Pg[:, low], st.P[:, low]))
             report[done] = e
-            assert e < 1e-5, (done, e)
+            assert e < 3e-6, (done, e)
     print("fp32c per-step error vs FP64 oracle:", report)
 
 
@@ -98,14 +101,16 @@ def test_fp32c_reduce64_variant_matches():
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    code = ("import numpy as np; from paper_1107_4107_b300 import inputs; "
-            "from paper_1107_4107_b300.api import ArnoldEnsemble as A; X,P=inputs.box(256, seed=3); "
-            "e=A(256, precision='fp32c'); e.set_state(X,P); e.iterate(100); "
-            "np.save('/dev/stdout', np.concatenate([e.indicator('dX'), e.indicator('P')]))")
+    import tempfile
     outs = []
-    for flag in ("0", "1"):
-        env = dict(os.environ, ARNOLD_FP32C_REDUCE64=flag, PYTHONPATH=root)
-        raw = subprocess.check_output([sys.executable, "-c", code], env=env, cwd=root)
-        import io
-        outs.append(np.load(io.BytesIO(raw)))
+    with tempfile.TemporaryDirectory() as tmp:
+        for flag in ("0", "1"):
+            path = os.path.join(tmp, f"r{flag}.npy")
+            code = ("import numpy as np; from paper_1107_4107_b300 import inputs; "
+                    "from paper_1107_4107_b300.api import ArnoldEnsemble as A; X,P=inputs.box(256, seed=3); "
+                    "e=A(256, precision='fp32c'); e.set_state(X,P); e.iterate(100); "
+                    f"np.save({path!r}, np.concatenate([e.indicator('dX'), e.indicator('P')]))")
+            env = dict(os.environ, ARNOLD_FP32C_REDUCE64=flag, PYTHONPATH=root)
+            subprocess.check_call([sys.executable, "-c", code], env=env, cwd=root)
+            outs.append(np.load(path))
     assert rel_err(outs[0], outs[1]) < 1e-6

@@ -7,7 +7,7 @@ table method vs libm, ~1 ulp) and the rotated coordinates used on the GPU
 |gpu - oracle| / (1 + |oracle|) on the unwrapped displacement, the momenta,
 the tangent vector and the indicators, at several step counts.  Chaotic
 trajectories amplify rounding like exp(lambda t), so all cells are compared
-over 100 steps (t = 6.3) and regular cells (tangent growth below e^7) up to
+over 100 steps (t = 6.3) and regular cells (tangent growth below e^5) up to
 1000 steps.
 """
 import math
@@ -120,9 +120,9 @@ def test_grid_parity_regular_cells_1000_steps(torch_cuda, E):
     assert all(v < TOL for k, v in errs.items() if k not in ("X", "dE_max")), errs
     ens.iterate(900)
     st.advance(900, threads=4)
-    # cells whose tangent grew less than e^7 over the run amplify rounding by less
+    # cells whose tangent grew less than e^5 over the run amplify rounding by less
     # than that; on them the two FP64 paths must still agree to the tolerance
-    regular = st.chi() * st.time() < 7.0
+    regular = st.chi() * st.time() < 5.0
     assert regular.mean() > 0.3
     for kind, ref in (("dX", st.unwrapped_displacement()), ("P", st.P), ("tangent", st.W)):
         got = ens.indicator(kind)
