@@ -7,8 +7,8 @@ table method vs libm, ~1 ulp) and the rotated coordinates used on the GPU
 |gpu - oracle| / (1 + |oracle|) on the unwrapped displacement, the momenta,
 the tangent vector and the indicators, at several step counts.  Chaotic
 trajectories amplify rounding like exp(lambda t), so all cells are compared
-over 100 steps (t = 6.3) and regular cells (tangent growth below e^5) up to
-1000 steps.
+over 100 steps (t = 6.3) and low-growth cells (tangent growth below e^5) up
+to 1000 steps from identical inputs.
 """
 import math
 
@@ -106,30 +106,42 @@ def test_other_schemes_parity(torch_cuda, scheme):
 
 
 @pytest.mark.parametrize("E", [400.0, 40.0])
-def test_grid_parity_regular_cells_1000_steps(torch_cuda, E):
-    """A 32 x 32 grid (several blocks, ragged last block with block 256): every cell
-    to 100 steps, regular cells to 1000 steps, each side from its own grid ICs."""
+def test_grid_parity_all_cells(torch_cuda, E):
+    """A 32 x 32 grid (several blocks, ragged last block): every cell to 100 steps,
+    each side from its own fixed-energy grid ICs (they differ by ~1 ulp in p_z)."""
     G = 32
     prm = oracle_params(R=100)
     st = oracle_grid_state(G, E, prm)
     ens = _ens(G * G)
     ens.init_grid(G, E)
-    ens.iterate(100)
-    st.advance(100, threads=4)
-    errs = compare_state(ens, st)
-    assert all(v < TOL for k, v in errs.items() if k not in ("X", "dE_max")), errs
-    ens.iterate(900)
-    st.advance(900, threads=4)
-    # cells whose tangent grew less than e^5 over the run amplify rounding by less
-    # than that; on them the two FP64 paths must still agree to the tolerance
-    regular = st.chi() * st.time() < 5.0
-    assert regular.mean() > 0.3
-    for kind, ref in (("dX", st.unwrapped_displacement()), ("P", st.P), ("tangent", st.W)):
-        got = ens.indicator(kind)
-        assert rel_err(got[:, regular], ref[:, regular]) < TOL, kind
-    assert rel_err(ens.indicator("chi")[regular], st.chi()[regular]) < TOL
-    cls = ens.indicator("class")
-    assert np.array_equal(cls[regular], st.classify()[regular])
+    for S in (10, 90):
+        ens.iterate(S)
+        st.advance(S, threads=4)
+        errs = compare_state(ens, st)
+        assert all(v < TOL for k, v in errs.items() if k not in ("X", "dE_max")), errs
+
+
+@pytest.mark.parametrize("lo,hi", [((10.0, 4.0, 25.0), (11.0, 5.0, 26.0)), ((4.0, 1.0, 6.0), (5.0, 2.0, 7.0))])
+def test_long_horizon_parity_low_growth_cells(torch_cuda, lo, hi):
+    """1000 steps from identical seeded inputs (E ~ 390 and E ~ 30): on cells whose
+    tangent grew less than e^5 the state, FTLE and V agree to 1e-12.  The tangent
+    vector itself depends on second derivatives of the flow, which grow like t^2
+    on regular orbits: a rounding random walk of ~1e-16 * sqrt(7000 kicks) ~ 1e-14
+    times t^2 ~ 4e3 at t = 63 gives ~4e-11, so its components are held to 1e-10."""
+    n = 1024
+    X, P = inputs.box(n, lo=lo, hi=hi, seed=13)
+    prm = oracle_params(R=100)
+    st = oracle.State(X, P, prm).advance(1000, threads=4)
+    ens = _ens(n)
+    ens.set_state(X, P)
+    ens.iterate(1000)
+    low = st.chi() * st.time() < 5.0
+    assert low.mean() > 0.3
+    for kind, ref in (("dX", st.unwrapped_displacement()), ("P", st.P), ("V", st.velocity())):
+        assert rel_err(ens.indicator(kind)[:, low], ref[:, low]) < TOL, kind
+    assert rel_err(ens.indicator("chi")[low], st.chi()[low]) < TOL
+    assert rel_err(ens.indicator("tangent")[:, low], st.W[:, low]) < 1e-10
+    assert np.array_equal(ens.indicator("class")[low], st.classify()[low])
 
 
 def test_window_velocity_parity(torch_cuda):
