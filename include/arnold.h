@@ -167,6 +167,27 @@ int arnold_stats_compute(arnold_ctx* ctx, arnold_stats* out);
 int arnold_stats_arrays(arnold_ctx* ctx, int64_t n, const double* chi, const double* dE,
                         const double* p, double t, double kappa, arnold_stats* out);
 
+/* Same statistics with no device allocation at all, and no context.  The
+ * paper has no counterpart: this exists for callers that must not call
+ * cudaMalloc -- for instance code running after another framework's caching
+ * allocator has reserved nearly all device memory, code that must avoid the
+ * device-wide synchronisation that cudaMalloc/cudaFree can cause, or a service
+ * whose memory budget is fixed at start-up.  The reduction's block partials
+ * live in a fixed ~1.7 MB array inside the library image (held by every GPU
+ * that loads the library until the process exits).
+ *   device, cuda_stream: where to run (stream NULL = legacy default stream).
+ *   n, chi, dE, p, t, kappa, out: as arnold_stats_arrays (device f64 inputs,
+ *   dE may be NULL, host output struct); synchronises the stream.
+ * The first call on a device looks up the array's device address (set-up);
+ * make that first call before any stream capture.  All calls share the array:
+ * calls whose kernels overlap on the GPU race and must be serialised by the
+ * caller.  Errors: EINVAL (NULL, n <= 0 or n > ARNOLD_NOALLOC_MAX_N, kappa <= 0,
+ * t == 0, bad device), EUNSUPPORTED, ECUDA. */
+#define ARNOLD_NOALLOC_MAX_N (1LL << 40)
+int arnold_stats_arrays_noalloc(int device, void* cuda_stream, int64_t n, const double* chi,
+                                const double* dE, const double* p, double t, double kappa,
+                                arnold_stats* out);
+
 /* Synchronise the context's stream; returns the first pending error. */
 int arnold_sync(arnold_ctx* ctx);
 

@@ -18,6 +18,7 @@ HOST, DEVICE = 0, 1
 IND = {"chi": 0, "V": 1, "dE": 2, "dE_max": 3, "class": 4, "X": 5, "P": 6, "dX": 7, "tangent": 8, "logsum": 9}
 IND_SHAPE = {"chi": 1, "V": 3, "dE": 1, "dE_max": 1, "class": 1, "X": 3, "P": 3, "dX": 3, "tangent": 6, "logsum": 1}
 HIST_BINS = 200
+NOALLOC_MAX_N = 1 << 40
 
 
 class ArnoldError(RuntimeError):
@@ -54,6 +55,8 @@ SIGNATURES = {
     "arnold_stats_compute": (ctypes.c_int, [vp, ctypes.POINTER(Stats)]),
     "arnold_stats_arrays": (ctypes.c_int, [vp, i64, vp, vp, vp, ctypes.c_double, ctypes.c_double,
                                            ctypes.POINTER(Stats)]),
+    "arnold_stats_arrays_noalloc": (ctypes.c_int, [ctypes.c_int, vp, i64, vp, vp, vp, ctypes.c_double,
+                                                   ctypes.c_double, ctypes.POINTER(Stats)]),
     "arnold_sync": (ctypes.c_int, [vp]),
     "arnold_launch_count": (i64, [vp]),
     "arnold_strerror": (ctypes.c_char_p, [ctypes.c_int]),

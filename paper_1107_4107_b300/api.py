@@ -161,6 +161,24 @@ def stats_dict(s) -> dict:
             "p_mean": np.array(list(s.p_mean)), "p_var": np.array(list(s.p_var)), "t": float(s.t)}
 
 
+def stats_arrays_noalloc(chi, dE, P, t: float, kappa: float = 10.0, device: int = 0, stream=None) -> dict:
+    """Ensemble statistics of device arrays without any device allocation (for
+    callers that cannot call cudaMalloc; see arnold_stats_arrays_noalloc in
+    include/arnold.h).  The library's fixed scratch is shared by all calls on a
+    device, so overlapping calls must be serialised by the caller."""
+    n = int(chi.shape[0])
+    if n > _lib.NOALLOC_MAX_N:
+        raise ValueError(f"n = {n} exceeds the allocation-free limit {_lib.NOALLOC_MAX_N}")
+    s = _lib.Stats()
+    pc, _ = _ptr_kind(chi)
+    pd, _ = _ptr_kind(dE)
+    pp, _ = _ptr_kind(P)
+    st = None if stream is None else ctypes.c_void_p(stream)
+    check(_lib.lib().arnold_stats_arrays_noalloc(device, st, n, pc, pd, pp, t, kappa, ctypes.byref(s)),
+          "arnold_stats_arrays_noalloc")
+    return stats_dict(s)
+
+
 def probe_peak(kind: str, device: int = 0) -> float:
     """Measured lane-operations/s of one pipe: 'dfma', 'ffma' or 'mufu'."""
     v = ctypes.c_double()
