@@ -188,6 +188,30 @@ int arnold_stats_arrays_noalloc(int device, void* cuda_stream, int64_t n, const 
                                 const double* dE, const double* p, double t, double kappa,
                                 arnold_stats* out);
 
+/* ---- differentiation ------------------------------------------------------
+ * Reverse-mode derivatives of the n_steps map of Sec. III (composite step,
+ * angles wrapped: wrapping adds constants and does not change derivatives)
+ * with respect to the initial state and to (h, eps).
+ *
+ * arnold_forward_ckpt: advance the ensemble n_steps >= 1 steps like
+ * arnold_iterate, storing the state every ckpt_every steps (0: ceil(sqrt(n)))
+ * in library-owned device memory (ceil(n_steps/C) + C states per trajectory).
+ * Any later set_state / init_grid / iterate discards the checkpoints.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int arnold_forward_ckpt(arnold_ctx* ctx, int64_t n_steps, int64_t ckpt_every);
+
+/* arnold_grad: given dL/dX_N and dL/dP_N ([3][n] f64 each, in the paper's
+ * coordinates; either may be NULL for zero) at the state reached by the last
+ * arnold_forward_ckpt, write dL/dX_0 and dL/dP_0 ([3][n] f64) and
+ * g_params[0] = dL/dh, g_params[1] = dL/deps (summed over trajectories).
+ * The state and checkpoints are left unchanged, so grad may be called again
+ * with another upstream gradient.  FP64 contexts differentiate in FP64;
+ * FP32C contexts recompute in compensated FP32 and differentiate in FP32
+ * (parameter sums in float pairs, then FP64).  ptr_kind applies to all five
+ * arrays.  Errors: EINVAL, ESTATE (no valid forward_ckpt), ECUDA. */
+int arnold_grad(arnold_ctx* ctx, const double* dL_dx, const double* dL_dp, double* g_x0, double* g_p0,
+                double* g_params, int ptr_kind);
+
 /* Synchronise the context's stream; returns the first pending error. */
 int arnold_sync(arnold_ctx* ctx);
 

@@ -57,6 +57,8 @@ SIGNATURES = {
                                            ctypes.POINTER(Stats)]),
     "arnold_stats_arrays_noalloc": (ctypes.c_int, [ctypes.c_int, vp, i64, vp, vp, vp, ctypes.c_double,
                                                    ctypes.c_double, ctypes.POINTER(Stats)]),
+    "arnold_forward_ckpt": (ctypes.c_int, [vp, i64, i64]),
+    "arnold_grad": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, ctypes.c_int]),
     "arnold_sync": (ctypes.c_int, [vp]),
     "arnold_launch_count": (i64, [vp]),
     "arnold_strerror": (ctypes.c_char_p, [ctypes.c_int]),

@@ -147,12 +147,70 @@ class ArnoldEnsemble:
               "arnold_stats_arrays")
         return stats_dict(s)
 
+    # -- differentiation --
+    def forward_ckpt(self, n_steps: int, ckpt_every: int = 0):
+        """Advance n_steps keeping sqrt(N) checkpoints for grad()."""
+        check(_lib.lib().arnold_forward_ckpt(self._h, int(n_steps), int(ckpt_every)), "arnold_forward_ckpt")
+
+    def grad(self, dL_dx=None, dL_dp=None, out_x=None, out_p=None):
+        """Reverse sweep: returns (dL/dX0, dL/dP0, dL/dh, dL/deps).  Upstream and
+        outputs are numpy (host) or torch CUDA tensors, [3][n] float64."""
+        like = dL_dp if dL_dp is not None else dL_dx
+        if like is None:
+            raise ValueError("need dL_dx or dL_dp")
+        if _is_torch(like) and like.is_cuda:
+            import torch
+            out_x = torch.empty((3, self.n), device=like.device, dtype=torch.float64) if out_x is None else out_x
+            out_p = torch.empty((3, self.n), device=like.device, dtype=torch.float64) if out_p is None else out_p
+            gpar = torch.empty(2, device=like.device, dtype=torch.float64)
+        else:
+            out_x = np.empty((3, self.n)) if out_x is None else out_x
+            out_p = np.empty((3, self.n)) if out_p is None else out_p
+            gpar = np.empty(2)
+        px, k = _ptr_kind(dL_dx) if dL_dx is not None else (None, None)
+        pp, k2 = _ptr_kind(dL_dp) if dL_dp is not None else (None, None)
+        kind = k if k is not None else k2
+        ox, _ = _ptr_kind(out_x)
+        op, _ = _ptr_kind(out_p)
+        og, _ = _ptr_kind(gpar)
+        check(_lib.lib().arnold_grad(self._h, px, pp, ox, op, og, kind), "arnold_grad")
+        return out_x, out_p, gpar[0], gpar[1]
+
     def debug_sincos(self, x, s, c, precision: str = "fp64"):
         px, _ = _ptr_kind(x)
         ps, _ = _ptr_kind(s)
         pc, _ = _ptr_kind(c)
         check(_lib.lib().arnold_debug_sincos(self._h, _lib.PRECISIONS[precision], int(x.shape[0]), px, ps, pc),
               "arnold_debug_sincos")
+
+
+def arnold_map(X0, P0, h, eps, n_steps: int, ckpt_every: int = 0, precision: str = "fp64", scheme: str = "yoshida6a"):
+    """Differentiable N-step map (X0, P0, h, eps) -> (X_N unwrapped, P_N) on torch CUDA
+    tensors; backward runs the CUDA adjoint with sqrt(N) checkpointing."""
+    import torch
+
+    class _ArnoldMap(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, X0, P0, h, eps):
+            n = X0.shape[1]
+            ens = ArnoldEnsemble(n, eps=float(eps), h=float(h), scheme=scheme, precision=precision, tangent=False,
+                                 device=X0.device.index or 0)
+            ens.set_state(X0.detach().contiguous(), P0.detach().contiguous())
+            ens.forward_ckpt(n_steps, ckpt_every)
+            dX = torch.empty_like(X0)
+            PN = torch.empty_like(P0)
+            ens.indicator("dX", out=dX)
+            ens.indicator("P", out=PN)
+            ctx.ens = ens
+            return X0.detach() + dX, PN
+
+        @staticmethod
+        def backward(ctx, gX, gP):
+            gx0, gp0, gh, ge = ctx.ens.grad(gX.contiguous(), gP.contiguous())
+            dev = gX.device
+            return gx0, gp0, gh.to(dev).reshape(()), ge.to(dev).reshape(())
+
+    return _ArnoldMap.apply(X0, P0, h, eps)
 
 
 def stats_dict(s) -> dict:

@@ -48,6 +48,17 @@ struct arnold_ctx {
   double* scratch = nullptr;   // [6][n] f64 read-out scratch (lazy)
   double* scratch2 = nullptr;  // [5][n] f64 statistics inputs (lazy)
   int reduce64 = 0;            // FP32C variant: FP64 mod-2pi reduction
+  // adjoint (forward_ckpt / grad)
+  void* ck = nullptr;          // [K][6][n] f64 or [K][12][n] f32
+  void* seg = nullptr;         // [C][...][n]
+  size_t ck_bytes = 0, seg_bytes = 0;
+  double* lam = nullptr;       // [6][n]
+  float* lamf = nullptr;       // [6][n]
+  double* gh = nullptr;        // [n]
+  double* ge = nullptr;        // [n]
+  double* sum_part = nullptr;  // [2 * stats_grid + 2]
+  int adj_valid = 0;
+  long long adj_N = 0, adj_C = 0, adj_K = 0;
 };
 
 namespace {
@@ -177,7 +188,7 @@ cudaError_t dalloc(T** p, size_t count) {
 void free_all(arnold_ctx* c) {
   void* ptrs[] = {c->s.st, c->s.tg, c->s.lap, c->s.lapref, c->s.ref, c->s.logsum, c->s.demax, c->s.e0, c->s.V,
                   c->f.hi, c->f.lo, c->f.tg, c->sc, c->th, c->scf, c->flags, c->partials, c->stats_out,
-                  c->scratch, c->scratch2};
+                  c->scratch, c->scratch2, c->ck, c->seg, c->lam, c->lamf, c->gh, c->ge, c->sum_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -365,6 +376,7 @@ int arnold_set_state(arnold_ctx* c, const double* x, const double* p, const doub
     a.w_in = c->prm.tangent ? w : nullptr;
   }
   ACHECK(cudaMemsetAsync(c->flags, 0, sizeof(int), c->stream));
+  c->adj_valid = 0;
   ACHECK(launch_set_state(a, grid_for(c, 256), 256, c->stream));
   c->launches++;
   c->steps = 0;
@@ -386,6 +398,7 @@ int arnold_init_grid(arnold_ctx* c, int64_t G, int64_t row0, double E, uint64_t 
   a.half_width = 0.9 * sqrt(E - 2.0 * fabs(c->prm.eps));
   a.raw_out = raw_out;
   ACHECK(cudaMemsetAsync(c->flags, 0, sizeof(int), c->stream));
+  c->adj_valid = 0;
   ACHECK(launch_init_grid(a, grid_for(c, 256), 256, c->stream));
   c->launches++;
   c->steps = 0;
@@ -394,6 +407,7 @@ int arnold_init_grid(arnold_ctx* c, int64_t G, int64_t row0, double E, uint64_t 
 
 int arnold_iterate(arnold_ctx* c, int64_t n_steps) {
   if (!c || n_steps < 0) return ARNOLD_EINVAL;
+  c->adj_valid = 0;
   if (fault_is("launch")) return ARNOLD_ECUDA;
   if (n_steps == 0) return ARNOLD_OK;
   ACHECK(cudaSetDevice(c->device));
@@ -512,6 +526,140 @@ int arnold_stats_compute(arnold_ctx* c, arnold_stats* out) {
   st = arnold_stats_arrays(c, c->n, chi, de, pp, (double)c->steps * c->prm.h, c->prm.chaos_kappa, out);
   if (st) return st;
   return check_flags(c);
+}
+
+static int ensure_bytes(void** p, size_t* have, size_t need) {
+  if (*have >= need && *p) return ARNOLD_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *have = 0;
+  ACHECK(cudaMalloc(p, need));
+  *have = need;
+  return ARNOLD_OK;
+}
+
+int arnold_forward_ckpt(arnold_ctx* c, int64_t n_steps, int64_t ckpt_every) {
+  if (!c || n_steps < 1 || ckpt_every < 0) return ARNOLD_EINVAL;
+  ACHECK(cudaSetDevice(c->device));
+  long long C = ckpt_every > 0 ? ckpt_every : (long long)ceil(sqrt((double)n_steps));
+  if (C > n_steps) C = n_steps;
+  const long long K = (n_steps + C - 1) / C;
+  const bool f32 = c->prm.precision == ARNOLD_FP32C;
+  const size_t n = (size_t)c->n;
+  const size_t per = f32 ? 12 * sizeof(float) * n : 6 * sizeof(double) * n;
+  int st = ensure_bytes(&c->ck, &c->ck_bytes, per * (size_t)K);
+  if (!st) st = ensure_bytes(&c->seg, &c->seg_bytes, per * (size_t)C);
+  if (st) return st;
+  if (!c->gh) ACHECK(dalloc(&c->gh, n));
+  if (!c->ge) ACHECK(dalloc(&c->ge, n));
+  if (!c->sum_part) ACHECK(dalloc(&c->sum_part, 2 * (size_t)c->stats_grid + 2));
+  if (f32) {
+    if (!c->lamf) ACHECK(dalloc(&c->lamf, 6 * n));
+  } else {
+    if (!c->lam) ACHECK(dalloc(&c->lam, 6 * n));
+  }
+  long long left = n_steps;
+  for (long long k = 0; k < K; ++k) {
+    char* dst = (char*)c->ck + per * (size_t)k;
+    if (f32) {
+      ACHECK(cudaMemcpyAsync(dst, c->f.hi, 6 * sizeof(float) * n, cudaMemcpyDeviceToDevice, c->stream));
+      ACHECK(cudaMemcpyAsync(dst + 6 * sizeof(float) * n, c->f.lo, 6 * sizeof(float) * n, cudaMemcpyDeviceToDevice,
+                             c->stream));
+    } else {
+      ACHECK(cudaMemcpyAsync(dst, c->s.st, per, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    const long long s = left < C ? left : C;
+    st = arnold_iterate(c, s);
+    if (st) return st;
+    left -= s;
+  }
+  c->adj_valid = 1;
+  c->adj_N = n_steps;
+  c->adj_C = C;
+  c->adj_K = K;
+  return ARNOLD_OK;
+}
+
+int arnold_grad(arnold_ctx* c, const double* dL_dx, const double* dL_dp, double* g_x0, double* g_p0,
+                double* g_params, int ptr_kind) {
+  if (!c || !g_x0 || !g_p0 || !g_params || (ptr_kind != ARNOLD_HOST && ptr_kind != ARNOLD_DEVICE))
+    return ARNOLD_EINVAL;
+  if (!c->adj_valid) return ARNOLD_ESTATE;
+  ACHECK(cudaSetDevice(c->device));
+  const bool f32 = c->prm.precision == ARNOLD_FP32C;
+  const size_t n = (size_t)c->n;
+  int st = device_scratch(c);
+  if (st) return st;
+  const double* dx = dL_dx;
+  const double* dp = dL_dp;
+  double* gx = g_x0;
+  double* gp = g_p0;
+  if (ptr_kind == ARNOLD_HOST) {   // stage through the [6][n] scratch
+    double* d = c->scratch;
+    if (dL_dx) ACHECK(cudaMemcpyAsync(d, dL_dx, 24 * n, cudaMemcpyHostToDevice, c->stream));
+    if (dL_dp) ACHECK(cudaMemcpyAsync(d + 3 * n, dL_dp, 24 * n, cudaMemcpyHostToDevice, c->stream));
+    dx = dL_dx ? d : nullptr;
+    dp = dL_dp ? d + 3 * n : nullptr;
+    gx = d;
+    gp = d + 3 * n;
+  }
+  const int g256 = grid_for(c, 256);
+  ACHECK(launch_adj_init(c->n, dx, dp, f32 ? nullptr : c->lam, f32 ? c->lamf : nullptr, c->gh, c->ge, g256,
+                         c->stream));
+  c->launches++;
+  AdjArgs a;
+  memset(&a, 0, sizeof a);
+  a.ck64 = f32 ? nullptr : (const double*)c->ck;
+  a.seg64 = f32 ? nullptr : (double*)c->seg;
+  a.ck32 = f32 ? (const float*)c->ck : nullptr;
+  a.seg32 = f32 ? (float*)c->seg : nullptr;
+  a.lam = c->lam;
+  a.lamf = c->lamf;
+  a.gh = c->gh;
+  a.ge = c->ge;
+  a.sc = c->sc;
+  a.th = c->th;
+  a.scf = c->scf;
+  a.n = c->n;
+  a.cf = make_coef(c->prm);
+  double w[9];
+  const int m = scheme_weights(c->prm.scheme, w);
+  for (int k = 0; k < m; ++k) {
+    a.ch[k] = 2.0 * w[k] * c->prm.eps;
+    a.ce[k] = 2.0 * w[k] * c->prm.h;
+    a.chf[k] = (float)a.ch[k];
+    a.cef[k] = (float)a.ce[k];
+  }
+  for (int k = 0; k <= m; ++k) {
+    const double left = k > 0 ? w[k - 1] : 0.0, right = k < m ? w[k] : 0.0;
+    a.cd[k] = 0.5 * (left + right);
+    a.cdf[k] = (float)a.cd[k];
+  }
+  long long g = (c->n + 127) / 128;
+  const long long cap = (long long)c->sms * 2;
+  if (g > cap) g = cap;
+  for (long long k = c->adj_K - 1; k >= 0; --k) {
+    a.k = (int)k;
+    const long long s0 = k * c->adj_C;
+    a.steps = (int)((c->adj_N - s0) < c->adj_C ? (c->adj_N - s0) : c->adj_C);
+    ACHECK(launch_adjoint_segment(a, c->prm.scheme, f32, (int)g, c->stream));
+    c->launches++;
+  }
+  ACHECK(launch_adj_finish(c->n, f32 ? nullptr : c->lam, f32 ? c->lamf : nullptr, gx, gp, g256, c->stream));
+  long long gs = (c->n + 255) / 256;
+  const int sg = (int)(gs < c->stats_grid ? gs : c->stats_grid);
+  double* out2 = c->sum_part + 2 * c->stats_grid;
+  ACHECK(launch_sum2(c->n, c->gh, c->ge, c->sum_part, sg, out2, c->stream));
+  c->launches += 3;
+  if (ptr_kind == ARNOLD_HOST) {
+    ACHECK(cudaMemcpyAsync(g_x0, gx, 24 * n, cudaMemcpyDeviceToHost, c->stream));
+    ACHECK(cudaMemcpyAsync(g_p0, gp, 24 * n, cudaMemcpyDeviceToHost, c->stream));
+    ACHECK(cudaMemcpyAsync(g_params, out2, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    ACHECK(cudaStreamSynchronize(c->stream));
+  } else {
+    ACHECK(cudaMemcpyAsync(g_params, out2, 2 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  }
+  return ARNOLD_OK;
 }
 
 int arnold_sync(arnold_ctx* c) {

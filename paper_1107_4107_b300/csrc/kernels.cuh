@@ -43,6 +43,36 @@ struct StatsPartial {   // one per block, merged in block order
   double mean[3], m2[3];
 };
 
+// One segment of the reverse sweep (adjoint.cu).
+struct AdjArgs {
+  const double* ck64;   // [K][6][n] FP64 checkpoints (rotated coordinates)
+  double* seg64;        // [C][6][n] step-start states of the current segment
+  const float* ck32;    // [K][12][n] FP32C checkpoints (6 hi, then 6 lo)
+  float* seg32;         // [C][12][n]
+  double* lam;          // [6][n] adjoint (FP64 path)
+  float* lamf;          // [6][n] adjoint (FP32C path)
+  double* gh;           // [n] per-trajectory dL/dh
+  double* ge;           // [n] per-trajectory dL/deps
+  const double2* sc;
+  const double* th;
+  const float2* scf;
+  long long n;
+  int k;                // segment index
+  int steps;            // steps in the segment
+  StepCoef cf;
+  double ch[9], ce[9];  // per kick: 2 w_k eps, 2 w_k h
+  double cd[10];        // per drift: sigma_k / h
+  float chf[9], cef[9], cdf[10];
+};
+
+cudaError_t launch_adjoint_segment(const AdjArgs& a, int scheme, bool fp32c, int grid, cudaStream_t st);
+cudaError_t launch_adj_init(long long n, const double* dx, const double* dp, double* lam, float* lamf, double* gh,
+                            double* ge, int grid, cudaStream_t st);
+cudaError_t launch_adj_finish(long long n, const double* lam, const float* lamf, double* gx, double* gp, int grid,
+                              cudaStream_t st);
+cudaError_t launch_sum2(long long n, const double* a, const double* b, double* part, int grid, double* out,
+                        cudaStream_t st);
+
 cudaError_t launch_set_state(const InitArgs& a, int grid, int block, cudaStream_t st);
 cudaError_t launch_init_grid(const InitArgs& a, int grid, int block, cudaStream_t st);
 cudaError_t launch_indicator(const ReadArgs& a, int grid, int block, cudaStream_t st);
