@@ -212,6 +212,59 @@ int arnold_forward_ckpt(arnold_ctx* ctx, int64_t n_steps, int64_t ckpt_every);
 int arnold_grad(arnold_ctx* ctx, const double* dL_dx, const double* dL_dp, double* g_x0, double* g_p0,
                 double* g_params, int ptr_kind);
 
+/* ---- batched persistent launch ----------------------------------------------
+ * Many parameter sets (the scans of Sec. IV repeated over a grid of (K, eps)),
+ * each a grid slice of initial actions with its own ensemble size and step
+ * count, advanced together by one CUDA-graph launch of persistent kernels in
+ * compensated FP32 (ARNOLD_FP32C).  Each set's trajectories are bit-identical
+ * to those of a single FP32C context with the same parameters. */
+typedef struct arnold_batch_set {
+  double   eps;       /* eps of Eq. 1                                         */
+  double   h;         /* composite step (K = eps h^2)                         */
+  double   E;         /* energy of the grid-slice ICs (E > 2|eps|)            */
+  int64_t  G;         /* grid width: the set holds G * G trajectories         */
+  int64_t  n_steps;   /* steps this set advances per arnold_batch_run         */
+  uint64_t seed;      /* SplitMix64 seed of the initial angles                */
+} arnold_batch_set;
+
+typedef struct arnold_batch_tuning {
+  int32_t block_size;       /* threads per block: multiple of 32 in [32, 256]        */
+  int32_t traj_per_thread;  /* 1 or 2 trajectories advanced interleaved per thread   */
+  int32_t renorm_every;     /* R >= 1 for every set                                  */
+  int32_t epoch_ms;         /* target GPU time of one persistent launch (ms)         */
+} arnold_batch_tuning;
+
+typedef struct arnold_batch arnold_batch;
+
+/* Defaults: block 256, 1 trajectory per thread, R 100, 200 ms epochs. */
+void arnold_batch_tuning_default(arnold_batch_tuning* t);
+
+/* Create a batch of n_sets sets (allocates every set's device state and plans
+ * the epochs).  tuning NULL = defaults.  Errors: EINVAL, ENOMEM, ECUDA,
+ * EUNSUPPORTED. */
+int arnold_batch_create(const arnold_batch_set* sets, int n_sets, int scheme, int tangent,
+                        const arnold_batch_tuning* tuning, int device, void* cuda_stream,
+                        arnold_batch** out);
+
+/* Grid-slice initial conditions for every set (as arnold_init_grid, row0 0). */
+int arnold_batch_init(arnold_batch* b);
+
+/* Advance every set by its n_steps: one graph launch (captured on first use;
+ * asynchronous on the batch's stream).  Repeated runs continue the sets. */
+int arnold_batch_run(arnold_batch* b);
+
+/* Indicator / statistics of one set (as arnold_indicator / arnold_stats_compute). */
+int arnold_batch_indicator(arnold_batch* b, int set, int kind, void* out, int ptr_kind);
+int arnold_batch_stats(arnold_batch* b, int set, arnold_stats* out);
+
+/* Plan size: epochs (persistent launches per run), work items per run, and
+ * map steps per run (sum over sets of G^2 n_steps). */
+int arnold_batch_info(const arnold_batch* b, int64_t* epochs, int64_t* items, int64_t* map_steps_per_run);
+
+int arnold_batch_sync(arnold_batch* b);
+int64_t arnold_batch_launch_count(const arnold_batch* b);
+void arnold_batch_destroy(arnold_batch* b);
+
 /* Synchronise the context's stream; returns the first pending error. */
 int arnold_sync(arnold_ctx* ctx);
 

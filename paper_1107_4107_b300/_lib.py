@@ -40,6 +40,16 @@ class Stats(ctypes.Structure):
                 ("p_mean", ctypes.c_double * 3), ("p_var", ctypes.c_double * 3), ("t", ctypes.c_double)]
 
 
+class BatchSet(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("h", ctypes.c_double), ("E", ctypes.c_double), ("G", ctypes.c_int64),
+                ("n_steps", ctypes.c_int64), ("seed", ctypes.c_uint64)]
+
+
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("block_size", ctypes.c_int32), ("traj_per_thread", ctypes.c_int32),
+                ("renorm_every", ctypes.c_int32), ("epoch_ms", ctypes.c_int32)]
+
+
 _lib = None
 vp = ctypes.c_void_p
 i64 = ctypes.c_int64
@@ -59,6 +69,17 @@ SIGNATURES = {
                                                    ctypes.c_double, ctypes.POINTER(Stats)]),
     "arnold_forward_ckpt": (ctypes.c_int, [vp, i64, i64]),
     "arnold_grad": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, ctypes.c_int]),
+    "arnold_batch_tuning_default": (None, [ctypes.POINTER(BatchTuning)]),
+    "arnold_batch_create": (ctypes.c_int, [ctypes.POINTER(BatchSet), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(BatchTuning), ctypes.c_int, vp, ctypes.POINTER(vp)]),
+    "arnold_batch_init": (ctypes.c_int, [vp]),
+    "arnold_batch_run": (ctypes.c_int, [vp]),
+    "arnold_batch_indicator": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int]),
+    "arnold_batch_stats": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(Stats)]),
+    "arnold_batch_info": (ctypes.c_int, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+    "arnold_batch_sync": (ctypes.c_int, [vp]),
+    "arnold_batch_launch_count": (i64, [vp]),
+    "arnold_batch_destroy": (None, [vp]),
     "arnold_sync": (ctypes.c_int, [vp]),
     "arnold_launch_count": (i64, [vp]),
     "arnold_strerror": (ctypes.c_char_p, [ctypes.c_int]),

@@ -213,6 +213,80 @@ def arnold_map(X0, P0, h, eps, n_steps: int, ckpt_every: int = 0, precision: str
     return _ArnoldMap.apply(X0, P0, h, eps)
 
 
+class ArnoldBatch:
+    """Many parameter sets advanced by one CUDA-graph launch (FP32C).
+
+    sets: list of dicts with eps, h, E, G, n_steps, seed (see arnold_batch_set).
+    tuning: dict with block_size, traj_per_thread, renorm_every, epoch_ms, or
+    None for the library defaults (paper_1107_4107_b300.tune picks one)."""
+
+    def __init__(self, sets, scheme: str = "yoshida6a", tangent: bool = True, tuning: dict | None = None,
+                 device: int = 0, stream=None):
+        L = _lib.lib()
+        arr = (_lib.BatchSet * len(sets))()
+        for k, q in enumerate(sets):
+            arr[k] = _lib.BatchSet(float(q["eps"]), float(q["h"]), float(q["E"]), int(q["G"]), int(q["n_steps"]),
+                                   int(q.get("seed", 0)))
+        tu = _lib.BatchTuning()
+        L.arnold_batch_tuning_default(ctypes.byref(tu))
+        for k, v in (tuning or {}).items():
+            setattr(tu, k, int(v))
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream(device).cuda_stream
+        h = ctypes.c_void_p()
+        check(L.arnold_batch_create(arr, len(sets), _lib.SCHEMES[scheme], int(bool(tangent)), ctypes.byref(tu), device,
+                                    ctypes.c_void_p(stream), ctypes.byref(h)), "arnold_batch_create")
+        self._h = h
+        self.sets = [dict(q) for q in sets]
+        self.tuning = {f: getattr(tu, f) for f, _ in _lib.BatchTuning._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.lib().arnold_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self):
+        check(_lib.lib().arnold_batch_init(self._h), "arnold_batch_init")
+
+    def run(self):
+        check(_lib.lib().arnold_batch_run(self._h), "arnold_batch_run")
+
+    def sync(self):
+        check(_lib.lib().arnold_batch_sync(self._h), "arnold_batch_sync")
+
+    @property
+    def launches(self) -> int:
+        return _lib.lib().arnold_batch_launch_count(self._h)
+
+    def info(self) -> dict:
+        e, i, m = _lib.i64(), _lib.i64(), _lib.i64()
+        check(_lib.lib().arnold_batch_info(self._h, ctypes.byref(e), ctypes.byref(i), ctypes.byref(m)),
+              "arnold_batch_info")
+        return {"epochs": e.value, "items": i.value, "map_steps_per_run": m.value}
+
+    def indicator(self, set_index: int, kind: str, out=None):
+        q = self.sets[set_index]
+        n = int(q["G"]) ** 2
+        rows = _lib.IND_SHAPE[kind]
+        if out is None:
+            out = np.empty((rows, n) if rows > 1 else (n,), dtype=np.uint8 if kind == "class" else np.float64)
+        po, ko = _ptr_kind(out)
+        check(_lib.lib().arnold_batch_indicator(self._h, set_index, _lib.IND[kind], po, ko), "arnold_batch_indicator")
+        return out
+
+    def stats(self, set_index: int) -> dict:
+        s = _lib.Stats()
+        check(_lib.lib().arnold_batch_stats(self._h, set_index, ctypes.byref(s)), "arnold_batch_stats")
+        return stats_dict(s)
+
+
 def stats_dict(s) -> dict:
     return {"hist": np.array(list(s.hist), dtype=np.int64), "under": int(s.under), "over": int(s.over),
             "chaotic": int(s.chaotic), "n": int(s.n), "dE_max": float(s.dE_max),

@@ -8,6 +8,7 @@
 #include <new>
 
 #include "kernels.cuh"
+#include "run32.cuh"
 
 namespace arnold {
 cudaError_t launch_iterate_fp32c_v(const IterArgs& a, int scheme, bool tangent, bool reduce64, int block, int grid,
@@ -260,6 +261,29 @@ size_t indicator_bytes(int kind, long long n) {
 }
 
 }  // namespace
+
+namespace arnold {
+// Accessors used by the batched launch (batch.cu).
+int ctx_run_args32(arnold_ctx* c, RunArgs32* ra, Coef32* cf, const float2** scf) {
+  if (c->prm.precision != ARNOLD_FP32C) return ARNOLD_EUNSUPPORTED;
+  ra->s = c->s;
+  ra->f = c->f;
+  ra->n = c->n;
+  ra->R = c->prm.renorm_every;
+  ra->W = c->prm.window;
+  ra->h = c->prm.h;
+  ra->eps = c->prm.eps;
+  ra->flags = c->flags;
+  *cf = coef32_from(make_coef(c->prm));
+  *scf = c->scf;
+  return ARNOLD_OK;
+}
+void ctx_add_steps(arnold_ctx* c, long long s) {
+  c->steps += s;
+  c->adj_valid = 0;
+}
+long long ctx_steps(arnold_ctx* c) { return c->steps; }
+}  // namespace arnold
 
 extern "C" {
 

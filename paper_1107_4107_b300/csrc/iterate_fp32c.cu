@@ -22,7 +22,7 @@
 // subtracting the FP64 2pi and splitting back (the FP64 reduction).
 #include <math.h>
 
-#include "step32.cuh"
+#include "run32.cuh"
 
 namespace arnold {
 
@@ -35,102 +35,21 @@ __global__ void __launch_bounds__(256) k_iterate_fp32c(IterArgs a, Tab32 tb) {
   for (int k = threadIdx.x; k <= tb.jmax; k += blockDim.x) ssc[k] = a.scf[k];
   __syncthreads();
 
+  RunArgs32 ra;
+  ra.s = a.s;
+  ra.f = a.f;
+  ra.n = a.n;
+  ra.R = a.R;
+  ra.W = a.W;
+  ra.h = a.h;
+  ra.eps = a.eps;
+  ra.flags = a.flags;
+  const Coef32 cf = coef32_from(a.cf);
   const long long n = a.n;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    Traj32 t;
-    t.u = {a.f.hi[i], a.f.lo[i]};
-    t.v = {a.f.hi[n + i], a.f.lo[n + i]};
-    t.z = {a.f.hi[2 * n + i], a.f.lo[2 * n + i]};
-    t.qu = {a.f.hi[3 * n + i], a.f.lo[3 * n + i]};
-    t.qv = {a.f.hi[4 * n + i], a.f.lo[4 * n + i]};
-    t.pz = {a.f.hi[5 * n + i], a.f.lo[5 * n + i]};
-    if (TAN) {
-      t.du = a.f.tg[i];
-      t.dv = a.f.tg[n + i];
-      t.dz = a.f.tg[2 * n + i];
-      t.dqu = a.f.tg[3 * n + i];
-      t.dqv = a.f.tg[4 * n + i];
-      t.dpz = a.f.tg[5 * n + i];
-    }
-    t.lu = a.s.lap[i];
-    t.lv = a.s.lap[n + i];
-    t.lz = a.s.lap[2 * n + i];
-    double logsum = TAN ? a.s.logsum[i] : 0.0;
-    double demax = a.s.demax[i];
-    int to_renorm = a.R - (int)(a.step0 % a.R);
-    long long to_window = a.W > 0 ? a.W - a.step0 % a.W : 0;
-    int bad = 0;
-
-#pragma unroll 1
-    for (int s = 0; s < a.nsteps; ++s) {
-      drift32<TAN, REDUCE64>(t, a.cf.sig_hi[0], a.cf.sig_lo[0]);
-#pragma unroll
-      for (int k = 0; k < M; ++k) {
-        kick32<TAN>(t, a.cf.k2f[k], a.cf.k4f[k], ssc, tb);
-        drift32<TAN, REDUCE64>(t, a.cf.sig_hi[k + 1], a.cf.sig_lo[k + 1]);
-      }
-      renorm(t.u); renorm(t.v); renorm(t.z);
-      renorm(t.qu); renorm(t.qv); renorm(t.pz);
-      if (--to_renorm == 0) {
-        to_renorm = a.R;
-        if (TAN) {
-          const float n2 = 0.5f * (t.du * t.du + t.dv * t.dv) + t.dz * t.dz +
-                           0.5f * (t.dqu * t.dqu + t.dqv * t.dqv) + t.dpz * t.dpz;
-          logsum += 0.5 * (double)__logf(n2);
-          const float inv = rsqrtf(n2);
-          t.du *= inv; t.dv *= inv; t.dz *= inv;
-          t.dqu *= inv; t.dqv *= inv; t.dpz *= inv;
-          if (!(n2 > 0.0f) || !isfinite(n2)) bad = 1;
-        }
-        float su, cu, sv, cv, sz, cz;
-        sincos_tab32(t.u, ssc, tb, su, cu);
-        sincos_tab32(t.v, ssc, tb, sv, cv);
-        sincos_tab32(t.z, ssc, tb, sz, cz);
-        const double kin = 0.25 * (pair_sq_d(t.qu) + pair_sq_d(t.qv)) + 0.5 * pair_sq_d(t.pz);
-        const double H = kin + a.eps * (double)((cu + cv) * (cz * cz));
-        const double dE = fabs(H - a.s.e0[i]);
-        demax = fmax(demax, dE);
-        if (!isfinite(dE)) bad = 1;
-      }
-      if (a.W > 0 && --to_window == 0) {
-        to_window = a.W;
-        const double inv_dt = 1.0 / ((double)a.W * a.h);
-        const double dU = (((double)t.u.hi + (double)t.u.lo) - a.s.ref[i]) + kTwoPi * (double)(t.lu - a.s.lapref[i]);
-        const double dV =
-            (((double)t.v.hi + (double)t.v.lo) - a.s.ref[n + i]) + kTwoPi * (double)(t.lv - a.s.lapref[n + i]);
-        const double dZ =
-            (((double)t.z.hi + (double)t.z.lo) - a.s.ref[2 * n + i]) + kTwoPi * (double)(t.lz - a.s.lapref[2 * n + i]);
-        a.s.V[i] = 0.5 * (dU + dV) * inv_dt;
-        a.s.V[n + i] = 0.5 * (dU - dV) * inv_dt;
-        a.s.V[2 * n + i] = dZ * inv_dt;
-        a.s.ref[i] = (double)t.u.hi + (double)t.u.lo;
-        a.s.ref[n + i] = (double)t.v.hi + (double)t.v.lo;
-        a.s.ref[2 * n + i] = (double)t.z.hi + (double)t.z.lo;
-        a.s.lapref[i] = t.lu; a.s.lapref[n + i] = t.lv; a.s.lapref[2 * n + i] = t.lz;
-      }
-    }
-
-    a.f.hi[i] = t.u.hi;          a.f.lo[i] = t.u.lo;
-    a.f.hi[n + i] = t.v.hi;      a.f.lo[n + i] = t.v.lo;
-    a.f.hi[2 * n + i] = t.z.hi;  a.f.lo[2 * n + i] = t.z.lo;
-    a.f.hi[3 * n + i] = t.qu.hi; a.f.lo[3 * n + i] = t.qu.lo;
-    a.f.hi[4 * n + i] = t.qv.hi; a.f.lo[4 * n + i] = t.qv.lo;
-    a.f.hi[5 * n + i] = t.pz.hi; a.f.lo[5 * n + i] = t.pz.lo;
-    if (TAN) {
-      a.f.tg[i] = t.du;
-      a.f.tg[n + i] = t.dv;
-      a.f.tg[2 * n + i] = t.dz;
-      a.f.tg[3 * n + i] = t.dqu;
-      a.f.tg[4 * n + i] = t.dqv;
-      a.f.tg[5 * n + i] = t.dpz;
-      a.s.logsum[i] = logsum;
-    }
-    a.s.lap[i] = t.lu;
-    a.s.lap[n + i] = t.lv;
-    a.s.lap[2 * n + i] = t.lz;
-    a.s.demax[i] = demax;
-    if (bad) atomicOr(a.flags, kFlagNonFinite);
+    const long long idx[1] = {i};
+    run_traj32<M, TAN, REDUCE64, 1>(ra, cf, idx, 1, a.step0, a.nsteps, ssc, tb);
   }
 }
 

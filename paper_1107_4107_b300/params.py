@@ -47,3 +47,30 @@ def grads_K_eps(g_h: float, g_eps: float, h: float, eps: float) -> tuple[float, 
     dh_dK = 1.0 / (2.0 * eps * h)          # dh/dK |_eps
     dh_deps = -h / (2.0 * eps)             # dh/deps |_K
     return g_h * dh_dK, g_eps + g_h * dh_deps
+
+
+def batch_sets(seed: int = 0, n_eps: int = 8, n_K: int = 8, eps_eff_range=(1e-5, 1e-1),
+               K_range=((0.005 * T_PERIOD) ** 2, (0.02 * T_PERIOD) ** 2), size_range=(1e3, 1e6),
+               steps_range=(1e4, 1e6), step_scale: float = 1.0, eps: float = 1.0) -> list[dict]:
+    """Parameter sets of the batched scan: an n_eps x n_K log grid of
+    (eps_eff, K) -> (E = 2 eps / eps_eff, h = sqrt(K / eps)); ensemble sizes
+    log-uniform in size_range (as G x G grids) and step counts log-uniform in
+    steps_range (times step_scale), drawn from SplitMix64(seed)."""
+    from .inputs import splitmix64, uniform01
+    import numpy as np
+    ee = np.geomspace(eps_eff_range[0], eps_eff_range[1], n_eps)
+    KK = np.geomspace(K_range[0], K_range[1], n_K)
+    m = n_eps * n_K
+    u = uniform01(splitmix64(seed, np.arange(2 * m, dtype=np.uint64))).reshape(2, m)
+    sizes = np.exp(np.log(size_range[0]) + u[0] * (np.log(size_range[1]) - np.log(size_range[0])))
+    steps = np.exp(np.log(steps_range[0]) + u[1] * (np.log(steps_range[1]) - np.log(steps_range[0])))
+    out = []
+    k = 0
+    for a in ee:
+        for K in KK:
+            G = max(8, int(round(math.sqrt(sizes[k]))))
+            out.append({"eps": eps, "h": h_for(K, eps), "E": energy_for(a, eps), "G": G,
+                        "n_steps": max(1, int(round(steps[k] * step_scale))), "seed": seed + k,
+                        "eps_eff": float(a), "K": float(K)})
+            k += 1
+    return out

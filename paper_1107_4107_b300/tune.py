@@ -1,0 +1,69 @@
+"""Autotuner of the batched persistent launch.
+
+Times each candidate (block size, trajectories per thread, renormalisation
+interval) on a scaled-down copy of the batch (G / 4, n_steps / 200) with CUDA
+events and keeps the fastest.  Results are cached per (GPU name, precision,
+scheme, tangent) in tune_cache.json next to this file.  The renormalisation
+interval only changes rounding of the FTLE (chi is independent of R) and the
+sampling interval of the energy error; candidates stay below R h lambda ~ 50,
+so the FP32 tangent cannot overflow between renormalisations.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CACHE = os.path.join(HERE, "tune_cache.json")
+CANDIDATES = [{"block_size": b, "traj_per_thread": t, "renorm_every": r, "epoch_ms": 200}
+              for b in (128, 256) for t in (1, 2) for r in (50, 100, 200)]
+
+
+def _key(scheme: str, tangent: bool) -> str:
+    import torch
+    return f"{torch.cuda.get_device_name()}|fp32c|{scheme}|{int(tangent)}"
+
+
+def scaled(sets, g_div: int = 4, step_div: int = 200):
+    return [dict(q, G=max(8, int(q["G"]) // g_div), n_steps=max(16, int(q["n_steps"]) // step_div)) for q in sets]
+
+
+def tune_batch(sets, scheme: str = "yoshida6a", tangent: bool = True, use_cache: bool = True,
+               candidates=None, verbose: bool = False) -> dict:
+    import torch
+    from .api import ArnoldBatch
+    key = _key(scheme, tangent)
+    cache = {}
+    if use_cache and os.path.exists(CACHE):
+        try:
+            cache = json.load(open(CACHE))
+        except ValueError:
+            cache = {}
+        if key in cache:
+            return cache[key]["tuning"]
+    sample = scaled(sets)
+    results = []
+    stream = torch.cuda.current_stream()
+    for cand in candidates or CANDIDATES:
+        b = ArnoldBatch(sample, scheme=scheme, tangent=tangent, tuning=cand)
+        b.init()
+        b.run()          # captures the graph, warms up
+        b.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.run()
+        e1.record(stream)
+        b.sync()
+        ms = e0.elapsed_time(e1)
+        rate = b.info()["map_steps_per_run"] / (ms * 1e-3)
+        results.append((rate, cand))
+        if verbose:
+            print(f"tune {cand}: {rate:.3e} map-steps/s")
+        b.close()
+    best = max(results, key=lambda r: r[0])
+    cache[key] = {"tuning": best[1], "rate_sample": best[0],
+                  "all": [{"tuning": c, "rate": r} for r, c in results]}
+    if use_cache:
+        json.dump(cache, open(CACHE, "w"), indent=1)
+    return best[1]
