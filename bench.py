@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--chunk", type=int, default=250, help="composite steps per bench step")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp32c", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the adjoint and batch legs")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
 
@@ -315,6 +316,9 @@ def main():
                  "agreement_note": "class agreement and histogram L1 vs FP64 are checked in tests/test_gpu_fp32c.py"}
         e3.close()
 
+    adjoint = None if args.no_extras else adjoint_leg(stream, local, barrier)
+    batch = None if args.no_extras else batch_leg(stream, local, barrier, args)
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -324,11 +328,78 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(args),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(gpu_launches),
-            "clocks": clk.summary(), "fp32c": fp32c,
+            "clocks": clk.summary(), "fp32c": fp32c, "adjoint": adjoint, "batch": batch,
             "probe": {"dfma_per_s": dfma, "ffma_per_s": ffma}}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def adjoint_leg(stream, device, barrier):
+    """Adjoint config: 65,536 trajectories from the seeded box, N = 1e4 steps,
+    sqrt(N) = 100 checkpoints, loss = mean final-momentum variance; FP64 and
+    FP32C.  Rate = map steps of the forward pass / (forward + reverse) time."""
+    import torch
+    from paper_1107_4107_b300 import inputs
+    from paper_1107_4107_b300.api import ArnoldEnsemble
+    n, N = 65536, 10000
+    X, P = inputs.box(n, seed=0)
+    Xd = torch.tensor(X, device="cuda")
+    Pd = torch.tensor(P, device="cuda")
+    out = {"config": "65,536 box trajectories (E ~ 390), N = 1e4, 100 checkpoints, variance loss"}
+    for prec in ("fp64", "fp32c"):
+        ens = ArnoldEnsemble(n, precision=prec, tangent=False, device=device, stream=stream.cuda_stream)
+        ens.set_state(Xd, Pd)
+        barrier()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        ens.forward_ckpt(N, 100)
+        e1.record(stream)
+        PN = torch.empty((3, n), device="cuda", dtype=torch.float64)
+        ens.indicator("P", out=PN)
+        up = (2.0 / 3.0) * (PN - PN.mean(dim=1, keepdim=True)) / n
+        gx, gp, gh, ge = ens.grad(dL_dp=up.contiguous())
+        e2.record(stream)
+        barrier()
+        fwd, tot = e0.elapsed_time(e1), e0.elapsed_time(e2)
+        out[prec] = {"value": n * N / (tot * 1e-3), "unit": "map-steps/s (forward + adjoint)",
+                     "forward_ms": fwd, "reverse_ms": tot - fwd, "dL_dh": float(gh), "dL_deps": float(ge)}
+        ens.close()
+    return out
+
+
+def batch_leg(stream, device, barrier, args):
+    """Batched config: 64 (K, eps_eff) sets on log grids, sizes log-U[1e3, 1e6]
+    (G x G grids), steps log-U[1e4, 1e6] scaled by 1/100 for the bench, FP32C,
+    one CUDA-graph launch per run, tuning from the autotuner."""
+    import torch
+    from paper_1107_4107_b300 import params, tune
+    from paper_1107_4107_b300.api import ArnoldBatch
+    sets = params.batch_sets(step_scale=0.01)
+    t0 = time.perf_counter()
+    tuning = tune.tune_batch(sets)
+    tune_s = time.perf_counter() - t0
+    b = ArnoldBatch(sets, tuning=tuning, device=device, stream=stream.cuda_stream)
+    b.init()
+    b.run()          # capture + warm-up run
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = b.launches
+    e0.record(stream)
+    b.run()
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    info = b.info()
+    out = {"value": info["map_steps_per_run"] / (ms * 1e-3), "unit": "map-steps/s", "ms_per_run": ms,
+           "sets": len(sets), "map_steps_per_run": info["map_steps_per_run"], "epochs": info["epochs"],
+           "items": info["items"], "tuning": tuning, "tune_seconds": tune_s, "graph_launches_per_run": 1,
+           "kernel_launches_per_run": b.launches - l0,
+           "config": "64 (K, eps_eff) pairs, eps_eff log-grid [1e-5, 1e-1], K log-grid [(0.005T)^2, (0.02T)^2], "
+                     "sizes log-U[1e3, 1e6], steps log-U[1e4, 1e6] x 0.01, FP32C"}
+    b.close()
+    return out
 
 
 def traffic_for(kernel: str):
