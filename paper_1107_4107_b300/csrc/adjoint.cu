@@ -153,14 +153,13 @@ __global__ void __launch_bounds__(128) k_adjoint_fp32c(AdjArgs a, Tab32 tb) {
       sg[3 * n + i] = t.qu.hi; sg[4 * n + i] = t.qv.hi; sg[5 * n + i] = t.pz.hi;
       sg[6 * n + i] = t.u.lo; sg[7 * n + i] = t.v.lo; sg[8 * n + i] = t.z.lo;
       sg[9 * n + i] = t.qu.lo; sg[10 * n + i] = t.qv.lo; sg[11 * n + i] = t.pz.lo;
-      drift32<false, false>(t, a.cf.sig_hi[0], a.cf.sig_lo[0]);
+      drift32<false>(t, a.cf.sig_hi[0], a.cf.sig_lo[0]);
 #pragma unroll
       for (int k = 0; k < M; ++k) {
         kick32<false>(t, a.cf.k2f[k], a.cf.k4f[k], ssc, tb);
-        drift32<false, false>(t, a.cf.sig_hi[k + 1], a.cf.sig_lo[k + 1]);
+        drift32<false>(t, a.cf.sig_hi[k + 1], a.cf.sig_lo[k + 1]);
       }
-      renorm(t.u); renorm(t.v); renorm(t.z);
-      renorm(t.qu); renorm(t.qv); renorm(t.pz);
+      end_step32<false>(t, tb);
     }
     float lu = a.lamf[i], lv = a.lamf[n + i], lz = a.lamf[2 * n + i];
     float lqu = a.lamf[3 * n + i], lqv = a.lamf[4 * n + i], lpz = a.lamf[5 * n + i];
@@ -177,13 +176,13 @@ __global__ void __launch_bounds__(128) k_adjoint_fp32c(AdjArgs a, Tab32 tb) {
       Pair xk[M][3];
       float qd[M + 1][3];
       qd[0][0] = t.qu.hi; qd[0][1] = t.qv.hi; qd[0][2] = t.pz.hi;
-      drift32<false, false>(t, a.cf.sig_hi[0], a.cf.sig_lo[0]);
+      drift32<false>(t, a.cf.sig_hi[0], a.cf.sig_lo[0]);
 #pragma unroll
       for (int k = 0; k < M; ++k) {
         xk[k][0] = t.u; xk[k][1] = t.v; xk[k][2] = t.z;
         kick32<false>(t, a.cf.k2f[k], a.cf.k4f[k], ssc, tb);
         qd[k + 1][0] = t.qu.hi; qd[k + 1][1] = t.qv.hi; qd[k + 1][2] = t.pz.hi;
-        drift32<false, false>(t, a.cf.sig_hi[k + 1], a.cf.sig_lo[k + 1]);
+        drift32<false>(t, a.cf.sig_hi[k + 1], a.cf.sig_lo[k + 1]);
       }
 #pragma unroll
       for (int k = M; k >= 0; --k) {
@@ -288,12 +287,12 @@ cudaError_t launch32(const AdjArgs& a, const Tab32& tb, int grid, cudaStream_t s
 
 }  // namespace
 
-void fp32_table_geometry(float* d, float* inv_d, int* jmax);
+void fp32_tab(Tab32* tb);
 
 cudaError_t launch_adjoint_segment(const AdjArgs& a, int scheme, bool fp32c, int grid, cudaStream_t st) {
   if (fp32c) {
     Tab32 tb;
-    fp32_table_geometry(&tb.d, &tb.inv_d, &tb.jmax);
+    fp32_tab(&tb);
     switch (scheme) {
       case ARNOLD_SCHEME_YOSHIDA6A: return launch32<7>(a, tb, grid, st);
       case ARNOLD_SCHEME_TRIPLEJUMP6: return launch32<9>(a, tb, grid, st);

@@ -14,16 +14,32 @@ namespace arnold {
 cudaError_t launch_iterate_fp32c_v(const IterArgs& a, int scheme, bool tangent, bool reduce64, int block, int grid,
                                    cudaStream_t st);
 
-// FP32 table geometry: D = 2 pi / 2048 rounded to 12 significant bits (so
-// j * D is exact in FP32 for j < 4096), jmax covers [0, 2pi + D/2].
-void fp32_table_geometry(float* d, float* inv_d, int* jmax) {
-  const double D = kTwoPi / 2048.0;
+// x rounded to `bits` significant bits.
+static long double round_bits(long double x, int bits) {
   int e;
-  const double m = frexp(D, &e);                   // D = m 2^e, m in [0.5, 1)
-  const double Dq = ldexp(floor(m * 4096.0 + 0.5) / 4096.0, e);
-  *d = (float)Dq;
-  *inv_d = (float)(1.0 / Dq);
-  *jmax = (int)ceil(kTwoPi / Dq) + 1;
+  const long double m = frexpl(x, &e);
+  return ldexpl(roundl(ldexpl(m, bits)), e - bits);
+}
+
+// FP32 table geometry (see Tab32 in step32.cuh): D = 2 pi / 2048 split into
+// d1 (7 significant bits) + d2 + d3, 2 pi split into c1 + c2 (18 bits each) + c3.
+void fp32_tab(Tab32* tb) {
+  const long double two_pi = 6.283185307179586476925286766559005768L;
+  const long double D = two_pi / 2048.0L;
+  const long double d1 = round_bits(D, 7);
+  const float d2 = (float)(D - d1);
+  const float d3 = (float)(D - d1 - (long double)d2);
+  tb->inv_d = (float)(1.0L / D);
+  tb->d1 = (float)d1;
+  tb->d2 = d2;
+  tb->d3 = d3;
+  tb->jmax = 2047;
+  tb->inv2pi = (float)(1.0L / two_pi);
+  const long double c1 = round_bits(two_pi, 18);
+  const long double c2 = round_bits(two_pi - c1, 18);
+  tb->c1 = (float)c1;
+  tb->c2 = (float)c2;
+  tb->c3 = (float)(two_pi - c1 - c2);
 }
 }  // namespace arnold
 
@@ -164,14 +180,14 @@ int build_tables(arnold_ctx* c) {
   free(hsc);
   free(hth);
   if (e != cudaSuccess) return cuda_status(e);
-  // FP32 table
-  float d, inv_d;
-  int jmax;
-  fp32_table_geometry(&d, &inv_d, &jmax);
+  // FP32 table: exactly periodic, (sin, cos)(2 pi j / 2048)
+  Tab32 tb;
+  fp32_tab(&tb);
+  const int jmax = tb.jmax;
   float2* hf = (float2*)malloc(sizeof(float2) * (jmax + 1));
   if (!hf) return ARNOLD_ENOMEM;
   for (int j = 0; j <= jmax; ++j) {
-    const long double t = (long double)j * (long double)d;
+    const long double t = (long double)j * (6.283185307179586476925286766559005768L / 2048.0L);
     hf[j].x = (float)sinl(t);
     hf[j].y = (float)cosl(t);
   }
@@ -564,6 +580,7 @@ static int ensure_bytes(void** p, size_t* have, size_t need) {
 
 int arnold_forward_ckpt(arnold_ctx* c, int64_t n_steps, int64_t ckpt_every) {
   if (!c || n_steps < 1 || ckpt_every < 0) return ARNOLD_EINVAL;
+  if (c->prm.precision == ARNOLD_FP32C && c->reduce64) return ARNOLD_EUNSUPPORTED;
   ACHECK(cudaSetDevice(c->device));
   long long C = ckpt_every > 0 ? ckpt_every : (long long)ceil(sqrt((double)n_steps));
   if (C > n_steps) C = n_steps;

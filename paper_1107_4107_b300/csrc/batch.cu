@@ -28,7 +28,7 @@ struct arnold_ctx;   // defined in api.cu
 
 namespace arnold {
 
-void fp32_table_geometry(float* d, float* inv_d, int* jmax);
+void fp32_tab(Tab32* tb);
 // Accessors into arnold_ctx (api.cu).
 int ctx_run_args32(arnold_ctx* c, RunArgs32* ra, Coef32* cf, const float2** scf);
 void ctx_add_steps(arnold_ctx* c, long long s);
@@ -365,7 +365,7 @@ int arnold_batch_run(arnold_batch* b) {
   if (e != cudaSuccess) return bstatus(e);
   if (!b->exec) {
     Tab32 tb;
-    fp32_table_geometry(&tb.d, &tb.inv_d, &tb.jmax);
+    fp32_tab(&tb);
     const size_t smem = (size_t)(tb.jmax + 1) * sizeof(float2);
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);

@@ -9,17 +9,17 @@
 //    (Dekker/FMA TwoProd) plus the cross terms, added with Knuth's TwoSum;
 //    the step size s itself is a float pair;
 //  * kick: the increment (FP32 force) added with TwoSum into the pair;
-//  * mod-2pi reduction after each drift against 2pi as a float pair
-//    (hi - C_hi is exact by Sterbenz' lemma), laps counted in int32;
-//  * pairs renormalised (Fast2Sum) once per composite step;
-//  * sincos by table lookup in FP32 (Tang's method, N = 2048,
-//    sin r ~ r, cos r ~ 1 - r^2/2 for |r| <= pi/2048; neglected terms
-//    < 7e-10) at the reduced argument (hi - theta_j) + lo, so the low word
-//    of the angle reaches the force;
+//  * sincos by lookup in an exactly periodic FP32 table (Tang's method,
+//    N = 2048, sin r ~ r, cos r ~ 1 - r^2/2, neglected terms < 7e-10) at the
+//    reduced argument ((hi - j D1) - j D2 - j D3) + lo, so angles need no
+//    reduction before a kick and the low word reaches the force;
+//  * pairs renormalised (Fast2Sum) once per composite step, and the angles
+//    reduced exactly (2 pi as three floats, TwoSum) once any exceeds 64 rad,
+//    laps counted in int32;
 //  * tangent vector in plain FP32; its renormalisation logs accumulated in
 //    FP64 every R steps, when the energy error is sampled in FP64 as well.
-// Variant REDUCE64: the wrap is done by widening the pair to FP64,
-// subtracting the FP64 2pi and splitting back (the FP64 reduction).
+// Variant REDUCE64: that reduction is done by widening the pair to FP64,
+// subtracting k times the FP64 2pi and splitting back (the FP64 reduction).
 #include <math.h>
 
 #include "run32.cuh"
@@ -89,12 +89,12 @@ __global__ void k_debug_sincos32(const double* x, double* s, double* c, long lon
 }  // namespace
 
 // Table geometry shared with the host table builder (api.cu).
-void fp32_table_geometry(float* d, float* inv_d, int* jmax);
+void fp32_tab(Tab32* tb);
 
 cudaError_t launch_iterate_fp32c_v(const IterArgs& a, int scheme, bool tangent, bool reduce64, int block, int grid,
                                    cudaStream_t st) {
   Tab32 tb;
-  fp32_table_geometry(&tb.d, &tb.inv_d, &tb.jmax);
+  fp32_tab(&tb);
   return reduce64 ? launch_scheme<true>(a, tb, scheme, tangent, block, grid, st)
                   : launch_scheme<false>(a, tb, scheme, tangent, block, grid, st);
 }
@@ -105,7 +105,7 @@ cudaError_t launch_iterate_fp32c(const IterArgs& a, int scheme, bool tangent, in
 
 int fp32c_blocks_per_sm(int scheme, bool tangent, int block) {
   Tab32 tb;
-  fp32_table_geometry(&tb.d, &tb.inv_d, &tb.jmax);
+  fp32_tab(&tb);
   const size_t smem = (size_t)(tb.jmax + 1) * sizeof(float2);
   int nb = 0;
   cudaError_t e = cudaSuccess;
@@ -129,7 +129,7 @@ int fp32c_blocks_per_sm(int scheme, bool tangent, int block) {
 cudaError_t launch_debug_sincos32(const double* x, double* s, double* c, long long n, const float2* scf,
                                   cudaStream_t st) {
   Tab32 tb;
-  fp32_table_geometry(&tb.d, &tb.inv_d, &tb.jmax);
+  fp32_tab(&tb);
   long long g = (n + 255) / 256;
   int grid = (int)(g > 4096 ? 4096 : (g < 1 ? 1 : g));
   k_debug_sincos32<<<grid, 256, 0, st>>>(x, s, c, n, scf, tb);

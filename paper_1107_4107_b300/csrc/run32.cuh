@@ -138,19 +138,16 @@ __device__ __forceinline__ void run_traj32(const RunArgs32& a, const Coef32& cf,
 #pragma unroll 1
   for (int s = 0; s < nsteps; ++s) {
 #pragma unroll
-    for (int r = 0; r < TPT; ++r) drift32<TAN, R64>(t[r], cf.sh[0], cf.sl[0]);
+    for (int r = 0; r < TPT; ++r) drift32<TAN>(t[r], cf.sh[0], cf.sl[0]);
 #pragma unroll
     for (int k = 0; k < M; ++k) {
 #pragma unroll
       for (int r = 0; r < TPT; ++r) kick32<TAN>(t[r], cf.k2[k], cf.k4[k], ssc, tb);
 #pragma unroll
-      for (int r = 0; r < TPT; ++r) drift32<TAN, R64>(t[r], cf.sh[k + 1], cf.sl[k + 1]);
+      for (int r = 0; r < TPT; ++r) drift32<TAN>(t[r], cf.sh[k + 1], cf.sl[k + 1]);
     }
 #pragma unroll
-    for (int r = 0; r < TPT; ++r) {
-      renorm(t[r].u); renorm(t[r].v); renorm(t[r].z);
-      renorm(t[r].qu); renorm(t[r].qv); renorm(t[r].pz);
-    }
+    for (int r = 0; r < TPT; ++r) end_step32<R64>(t[r], tb);
     if (--to_renorm == 0) {
       to_renorm = a.R;
 #pragma unroll

@@ -1,14 +1,11 @@
 // Compensated-FP32 building blocks (float pairs, TwoSum/TwoProd updates,
-// float-pair mod-2pi wraps, FP32 table sincos, drift/kick) shared by the
-// iterate and adjoint kernels so that recomputed states are bit-identical.
+// exact float-pair mod-2pi reduction, FP32 periodic-table sincos, drift/kick)
+// shared by the iterate, batch and adjoint kernels so that recomputed states
+// are bit-identical.
 #pragma once
 #include "devmath.cuh"
 
 namespace arnold {
-
-constexpr float kC2PiHi = 6.28318548202514648438f;        // float nearest 2pi
-constexpr float kC2PiLo = -1.74845553146951715462e-07f;   // 2pi - kC2PiHi, rounded
-constexpr int kC2PiHiBits = 0x40C90FDB;
 
 struct Pair { float hi, lo; };
 
@@ -53,70 +50,85 @@ __device__ __forceinline__ void drift_comp(Pair& x, float sh, float sl, const Pa
   x.lo = __fadd_rn(x.lo, __fadd_rn(t, e));
 }
 
-template <bool REDUCE64>
-__device__ __forceinline__ void wrap_pair(Pair& x, int& lap) {
-  const int b = __float_as_int(x.hi);
-  if (b >= kC2PiHiBits || b < 0) {
-#pragma unroll 1
-    for (int it = 0; it < 4096; ++it) {
-      const int bb = __float_as_int(x.hi);
-      if (bb >= kC2PiHiBits) {
-        if (REDUCE64) {
-          const double d = ((double)x.hi + (double)x.lo) - kTwoPi;
-          x.hi = __double2float_rn(d);
-          x.lo = __double2float_rn(d - (double)x.hi);
-        } else {
-          x.hi = __fsub_rn(x.hi, kC2PiHi);   // exact (Sterbenz)
-          x.lo = __fsub_rn(x.lo, kC2PiLo);
-        }
-        lap += 1;
-      } else if (bb < 0) {
-        if (REDUCE64) {
-          const double d = ((double)x.hi + (double)x.lo) + kTwoPi;
-          x.hi = __double2float_rn(d);
-          x.lo = __double2float_rn(d - (double)x.hi);
-        } else {
-          float s, e;
-          two_sum(x.hi, kC2PiHi, s, e);
-          x.hi = s;
-          x.lo = __fadd_rn(x.lo, __fadd_rn(e, kC2PiLo));
-        }
-        lap -= 1;
-      } else {
-        break;
-      }
-    }
-  }
-}
-
-// FP32 table sincos of the pair value hi + lo, hi in [-D/2, 2pi + D/2].
+// FP32 table sincos (Tang's method) with an exactly periodic table:
+// theta_j = j D, D = 2 pi / 2048, table[j mod 2048] = (sin, cos)(2 pi j / 2048)
+// rounded from long-double libm.  D is split D1 + D2 + D3 (D1 with 7
+// significant bits, so j D1 is exact for |j| < 2^17) and the reduced argument
+// r = ((hi - j D1) - j D2 - j D3) + lo is formed with one rounding per FMA at
+// |r| <= D/2; angles therefore need no reduction before a kick as long as
+// |hi| < 2^17 D ~ 400.  sin r ~ r, cos r ~ 1 - r^2/2 (neglected terms < 7e-10).
+// 2 pi = C1 + C2 + C3 (C1, C2 with 18 significant bits) serves the exact
+// reduction below.
 struct Tab32 {
-  float inv_d;     // 1 / D
-  float d;         // D (12 significant bits: j * D exact in FP32)
-  int jmax;        // last table index
+  float inv_d;       // 1 / D
+  float d1, d2, d3;  // D = d1 + d2 + d3
+  int jmax;          // 2047: last table index and index mask
+  float inv2pi;      // 1 / (2 pi)
+  float c1, c2, c3;  // 2 pi = c1 + c2 + c3
 };
 
 __device__ __forceinline__ void sincos_tab32(const Pair& x, const float2* __restrict__ sc, const Tab32& tb, float& s,
                                              float& c) {
-  const float t = fmaf(x.hi, tb.inv_d, 12582912.0f);       // 1.5 * 2^23
+  const float t = fmaf(x.hi, tb.inv_d, 12582912.0f);       // 1.5 * 2^23: rint(hi / D) in the low bits
   const float jf = __fsub_rn(t, 12582912.0f);
-  int j = __float_as_int(t) - 0x4B400000;
-  j = min(max(j, 0), tb.jmax);
-  const float r = __fadd_rn(fmaf(-jf, tb.d, x.hi), x.lo);   // (hi - theta_j) exact, then + lo
+  const int j = (__float_as_int(t) - 0x4B400000) & tb.jmax;
+  float r = fmaf(-jf, tb.d1, x.hi);                          // exact
+  r = fmaf(-jf, tb.d2, r);
+  r = fmaf(-jf, tb.d3, r);
+  r = __fadd_rn(r, x.lo);
   const float2 e = sc[j];
   const float cm = __fmul_rn(-0.5f, __fmul_rn(r, r));
   s = fmaf(e.y, r, fmaf(e.x, cm, e.x));
   c = fmaf(-e.x, r, fmaf(e.y, cm, e.y));
 }
 
-template <bool TAN, bool REDUCE64>
+// Exact removal of k = rint(x / 2 pi) turns from an angle pair, laps += k.
+// hi - k C1 and k C2 are exact (|k| < 64), the TwoSum keeps the second
+// subtraction exact, so the only rounding is at the level of lo.
+// REDUCE64 variant: the same in FP64 (widen, subtract k * 2pi, split).
+template <bool REDUCE64>
+__device__ __forceinline__ void reduce_angle(Pair& x, int& lap, const Tab32& tb) {
+  if (REDUCE64) {
+    const double d = (double)x.hi + (double)x.lo;
+    const double k = rint(d * (1.0 / kTwoPi));
+    const double r = fma(-k, kTwoPi, d);
+    x.hi = __double2float_rn(r);
+    x.lo = __double2float_rn(r - (double)x.hi);
+    lap += (int)k;
+  } else {
+    const float t = fmaf(x.hi, tb.inv2pi, 12582912.0f);
+    const float kf = __fsub_rn(t, 12582912.0f);
+    const int k = __float_as_int(t) - 0x4B400000;
+    const float h1 = fmaf(-kf, tb.c1, x.hi);
+    float s, e;
+    two_sum(h1, __fmul_rn(-kf, tb.c2), s, e);
+    const float lo = fmaf(-kf, tb.c3, __fadd_rn(x.lo, e));
+    fast_two_sum(s, lo, x.hi, x.lo);
+    lap += k;
+  }
+}
+
+// End of a composite step: renormalise all pairs; reduce the angles once any
+// of them has grown past 64 rad (every few tens of steps at E = 400), which
+// keeps every kick's argument within the table's exact range for h |q| < 300.
+template <bool REDUCE64>
+__device__ __forceinline__ void end_step32(Traj32& t, const Tab32& tb) {
+  renorm(t.u); renorm(t.v); renorm(t.z);
+  renorm(t.qu); renorm(t.qv); renorm(t.pz);
+  const int big = max(max(__float_as_int(t.u.hi) & 0x7FFFFFFF, __float_as_int(t.v.hi) & 0x7FFFFFFF),
+                      __float_as_int(t.z.hi) & 0x7FFFFFFF);
+  if (big > 0x42800000) {   // |angle| > 64
+    reduce_angle<REDUCE64>(t.u, t.lu, tb);
+    reduce_angle<REDUCE64>(t.v, t.lv, tb);
+    reduce_angle<REDUCE64>(t.z, t.lz, tb);
+  }
+}
+
+template <bool TAN>
 __device__ __forceinline__ void drift32(Traj32& t, float sh, float sl) {
   drift_comp(t.u, sh, sl, t.qu);
   drift_comp(t.v, sh, sl, t.qv);
   drift_comp(t.z, sh, sl, t.pz);
-  wrap_pair<REDUCE64>(t.u, t.lu);
-  wrap_pair<REDUCE64>(t.v, t.lv);
-  wrap_pair<REDUCE64>(t.z, t.lz);
   if (TAN) {
     t.du = fmaf(sh, t.dqu, t.du);
     t.dv = fmaf(sh, t.dqv, t.dv);
