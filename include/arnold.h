@@ -84,7 +84,7 @@ typedef struct arnold_params {
   int32_t renorm_every;  /* R >= 1: tangent renormalisation / energy sampling interval      */
   int64_t window;        /* W >= 0: steps per averaging window of V; 0 = whole run          */
   double  chaos_kappa;   /* kappa > 0 of the regular/chaotic threshold (default 10)         */
-  int32_t block_size;    /* threads per block, multiple of 32 in [32, 512]; 0 = default    */
+  int32_t block_size;    /* threads per block, multiple of 32 in [32, 256]; 0 = default    */
   int32_t launch_steps;  /* max composite steps per kernel launch; 0 = automatic (~0.2 s)   */
 } arnold_params;
 

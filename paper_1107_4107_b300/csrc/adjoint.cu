@@ -11,11 +11,12 @@
 //                      dL/dh += 2 d_k eps F;  dL/deps += 2 d_k h F
 // States are recomputed from checkpoints: the forward run stores the state
 // every C steps (C ~ sqrt(N)); for each segment, in reverse, the kernel
-// re-runs the segment storing every step-start state in a scratch buffer,
-// then for each step (reverse order) re-runs its substeps keeping the kick
-// positions and drift momenta in registers, and sweeps them backwards.  The
-// recomputation uses the same device functions as the forward kernels, so it
-// reproduces the forward states bit for bit.
+// re-runs the segment (same device functions as the forward kernels, so bit
+// for bit) storing the state after every step in a scratch buffer; then, step
+// by step in reverse, it runs each step backwards from its stored end state
+// (reverse drift X -= s q, reverse kick q -= increment(X), sharing the kick's
+// sincos with the adjoint), so the positions and momenta inside a step are
+// regained to rounding without storing them.
 #include "kernels.cuh"
 #include "step32.cuh"
 #include "step64.cuh"
@@ -24,14 +25,15 @@ namespace arnold {
 
 namespace {
 
-template <int M>
+// Adjoint of kick k at X (sincos shared): lambda_X += J^T lambda_q and the
+// parameter terms; then the kick is undone, q -= increment(X).
 __device__ __forceinline__ void adj_kick64(double& lu, double& lv, double& lz, double lqu, double lqv, double lpz,
-                                           double u, double v, double z, double k2, double k4, double ch, double ce,
-                                           double& gh, double& ge, const double2* sc, const double* th) {
+                                           Traj64& t, double k2, double k4, double ch, double ce, double& gh,
+                                           double& ge, const double2* sc, const double* th) {
   double su, cu, sv, cv, sz, cz;
-  sincos_tab64(u, sc, th, su, cu);
-  sincos_tab64(v, sc, th, sv, cv);
-  sincos_tab64(z, sc, th, sz, cz);
+  sincos_tab64(t.u, sc, th, su, cu);
+  sincos_tab64(t.v, sc, th, sv, cv);
+  sincos_tab64(t.z, sc, th, sz, cz);
   const double g = cz * cz, sh = sz * cz;
   const double G = k2 * g, Sp = k2 * sh, A = cu + cv;
   const double F = fma(lqu * su, g, fma(lqv * sv, g, lpz * (sh * A)));
@@ -41,10 +43,38 @@ __device__ __forceinline__ void adj_kick64(double& lu, double& lv, double& lz, d
   lu = fma(G * cu, lqu, fma(-Sp * su, lpz, lu));
   lv = fma(G * cv, lqv, fma(-Sp * sv, lpz, lv));
   lz = fma(-2.0 * Sp, fma(su, lqu, sv * lqv), fma(Z, lpz, lz));
+  t.qu = fma(-G, su, t.qu);
+  t.qv = fma(-G, sv, t.qv);
+  t.pz = fma(-Sp, A, t.pz);
+}
+
+// Reverse sweep of one step: from the step's end state, undo drift m, kick
+// m-1, ..., drift 0 (positions and momenta within the step are regained by
+// running the step backwards; they match the forward ones to rounding),
+// applying the adjoint of each operation on the way.
+template <int M>
+__device__ __forceinline__ void reverse_step64(Traj64& t, double& lu, double& lv, double& lz, double& lqu,
+                                               double& lqv, double& lpz, double& gh, double& ge, const AdjArgs& a,
+                                               const double2* sc, const double* th) {
+#pragma unroll
+  for (int k = M; k >= 0; --k) {
+    const double sg = a.cf.sig[k];
+    gh = fma(a.cd[k], fma(lu, t.qu, fma(lv, t.qv, lz * t.pz)), gh);
+    lqu = fma(sg, lu, lqu);
+    lqv = fma(sg, lv, lqv);
+    lpz = fma(sg, lz, lpz);
+    t.u = fma(-sg, t.qu, t.u);
+    t.v = fma(-sg, t.qv, t.v);
+    t.z = fma(-sg, t.pz, t.z);
+    wrap_angle(t.u, t.lu);
+    wrap_angle(t.v, t.lv);
+    wrap_angle(t.z, t.lz);
+    if (k > 0) adj_kick64(lu, lv, lz, lqu, lqv, lpz, t, a.cf.k2[k - 1], a.cf.k4[k - 1], a.ch[k - 1], a.ce[k - 1], gh, ge, sc, th);
+  }
 }
 
 template <int M>
-__global__ void __launch_bounds__(128) k_adjoint_fp64(AdjArgs a) {
+__global__ void __launch_bounds__(256) k_adjoint_fp64(AdjArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   double2* ssc = reinterpret_cast<double2*>(smem);
   double* sth = reinterpret_cast<double*>(smem + kTabEntries * sizeof(double2));
@@ -56,20 +86,20 @@ __global__ void __launch_bounds__(128) k_adjoint_fp64(AdjArgs a) {
     t.u = ck[i]; t.v = ck[n + i]; t.z = ck[2 * n + i];
     t.qu = ck[3 * n + i]; t.qv = ck[4 * n + i]; t.pz = ck[5 * n + i];
     t.lu = t.lv = t.lz = 0;
-    // pass 1: step-start states of the segment
+    // pass 1: the state after every step of the segment (slot s = end of step s)
 #pragma unroll 1
     for (int s = 0; s < a.steps; ++s) {
-      double* sg = a.seg64 + (long long)s * 6 * n;
-      sg[i] = t.u; sg[n + i] = t.v; sg[2 * n + i] = t.z;
-      sg[3 * n + i] = t.qu; sg[4 * n + i] = t.qv; sg[5 * n + i] = t.pz;
       drift64<false>(t, a.cf.sig[0]);
 #pragma unroll
       for (int k = 0; k < M; ++k) {
         kick64<false>(t, a.cf.k2[k], a.cf.k4[k], ssc, sth);
         drift64<false>(t, a.cf.sig[k + 1]);
       }
+      double* sg = a.seg64 + (long long)s * 6 * n;
+      sg[i] = t.u; sg[n + i] = t.v; sg[2 * n + i] = t.z;
+      sg[3 * n + i] = t.qu; sg[4 * n + i] = t.qv; sg[5 * n + i] = t.pz;
     }
-    // pass 2: reverse sweep
+    // pass 2: reverse sweep, each step run backwards from its stored end state
     double lu = a.lam[i], lv = a.lam[n + i], lz = a.lam[2 * n + i];
     double lqu = a.lam[3 * n + i], lqv = a.lam[4 * n + i], lpz = a.lam[5 * n + i];
     double gh = a.gh[i], ge = a.ge[i];
@@ -78,27 +108,7 @@ __global__ void __launch_bounds__(128) k_adjoint_fp64(AdjArgs a) {
       const double* sg = a.seg64 + (long long)s * 6 * n;
       t.u = sg[i]; t.v = sg[n + i]; t.z = sg[2 * n + i];
       t.qu = sg[3 * n + i]; t.qv = sg[4 * n + i]; t.pz = sg[5 * n + i];
-      double xk[M][3], qd[M + 1][3];
-      qd[0][0] = t.qu; qd[0][1] = t.qv; qd[0][2] = t.pz;
-      drift64<false>(t, a.cf.sig[0]);
-#pragma unroll
-      for (int k = 0; k < M; ++k) {
-        xk[k][0] = t.u; xk[k][1] = t.v; xk[k][2] = t.z;
-        kick64<false>(t, a.cf.k2[k], a.cf.k4[k], ssc, sth);
-        qd[k + 1][0] = t.qu; qd[k + 1][1] = t.qv; qd[k + 1][2] = t.pz;
-        drift64<false>(t, a.cf.sig[k + 1]);
-      }
-#pragma unroll
-      for (int k = M; k >= 0; --k) {
-        // drift k (its momentum qd[k])
-        gh = fma(a.cd[k], fma(lu, qd[k][0], fma(lv, qd[k][1], lz * qd[k][2])), gh);
-        lqu = fma(a.cf.sig[k], lu, lqu);
-        lqv = fma(a.cf.sig[k], lv, lqv);
-        lpz = fma(a.cf.sig[k], lz, lpz);
-        if (k > 0)
-          adj_kick64<M>(lu, lv, lz, lqu, lqv, lpz, xk[k - 1][0], xk[k - 1][1], xk[k - 1][2], a.cf.k2[k - 1],
-                        a.cf.k4[k - 1], a.ch[k - 1], a.ce[k - 1], gh, ge, ssc, sth);
-      }
+      reverse_step64<M>(t, lu, lv, lz, lqu, lqv, lpz, gh, ge, a, ssc, sth);
     }
     a.lam[i] = lu; a.lam[n + i] = lv; a.lam[2 * n + i] = lz;
     a.lam[3 * n + i] = lqu; a.lam[4 * n + i] = lqv; a.lam[5 * n + i] = lpz;
@@ -112,12 +122,12 @@ __global__ void __launch_bounds__(128) k_adjoint_fp64(AdjArgs a) {
 __device__ __forceinline__ void acc_pair(Pair& acc, float x) { add_comp(acc, x); }
 
 __device__ __forceinline__ void adj_kick32(float& lu, float& lv, float& lz, float lqu, float lqv, float lpz,
-                                           const Pair& u, const Pair& v, const Pair& z, float k2, float k4, float ch,
-                                           float ce, Pair& gh, Pair& ge, const float2* sc, const Tab32& tb) {
+                                           Traj32& t, float k2, float k4, float ch, float ce, Pair& gh, Pair& ge,
+                                           const float2* sc, const Tab32& tb) {
   float su, cu, sv, cv, sz, cz;
-  sincos_tab32(u, sc, tb, su, cu);
-  sincos_tab32(v, sc, tb, sv, cv);
-  sincos_tab32(z, sc, tb, sz, cz);
+  sincos_tab32(t.u, sc, tb, su, cu);
+  sincos_tab32(t.v, sc, tb, sv, cv);
+  sincos_tab32(t.z, sc, tb, sz, cz);
   const float g = cz * cz, sh = sz * cz;
   const float G = k2 * g, Sp = k2 * sh, A = cu + cv;
   const float F = fmaf(lqu * su, g, fmaf(lqv * sv, g, lpz * (sh * A)));
@@ -127,10 +137,13 @@ __device__ __forceinline__ void adj_kick32(float& lu, float& lv, float& lz, floa
   lu = fmaf(G * cu, lqu, fmaf(-Sp * su, lpz, lu));
   lv = fmaf(G * cv, lqv, fmaf(-Sp * sv, lpz, lv));
   lz = fmaf(-2.0f * Sp, fmaf(su, lqu, sv * lqv), fmaf(Z, lpz, lz));
+  add_comp(t.qu, -(G * su));
+  add_comp(t.qv, -(G * sv));
+  add_comp(t.pz, -(Sp * A));
 }
 
 template <int M>
-__global__ void __launch_bounds__(128) k_adjoint_fp32c(AdjArgs a, Tab32 tb) {
+__global__ void __launch_bounds__(256) k_adjoint_fp32c(AdjArgs a, Tab32 tb) {
   extern __shared__ __align__(16) unsigned char smem[];
   float2* ssc = reinterpret_cast<float2*>(smem);
   for (int k = threadIdx.x; k <= tb.jmax; k += blockDim.x) ssc[k] = a.scf[k];
@@ -146,13 +159,9 @@ __global__ void __launch_bounds__(128) k_adjoint_fp32c(AdjArgs a, Tab32 tb) {
     t.qv = {ck[4 * n + i], ck[10 * n + i]};
     t.pz = {ck[5 * n + i], ck[11 * n + i]};
     t.lu = t.lv = t.lz = 0;
+    // pass 1: the state after every step of the segment
 #pragma unroll 1
     for (int s = 0; s < a.steps; ++s) {
-      float* sg = a.seg32 + (long long)s * 12 * n;
-      sg[i] = t.u.hi; sg[n + i] = t.v.hi; sg[2 * n + i] = t.z.hi;
-      sg[3 * n + i] = t.qu.hi; sg[4 * n + i] = t.qv.hi; sg[5 * n + i] = t.pz.hi;
-      sg[6 * n + i] = t.u.lo; sg[7 * n + i] = t.v.lo; sg[8 * n + i] = t.z.lo;
-      sg[9 * n + i] = t.qu.lo; sg[10 * n + i] = t.qv.lo; sg[11 * n + i] = t.pz.lo;
       drift32<false>(t, a.cf.sig_hi[0], a.cf.sig_lo[0]);
 #pragma unroll
       for (int k = 0; k < M; ++k) {
@@ -160,6 +169,11 @@ __global__ void __launch_bounds__(128) k_adjoint_fp32c(AdjArgs a, Tab32 tb) {
         drift32<false>(t, a.cf.sig_hi[k + 1], a.cf.sig_lo[k + 1]);
       }
       end_step32<false>(t, tb);
+      float* sg = a.seg32 + (long long)s * 12 * n;
+      sg[i] = t.u.hi; sg[n + i] = t.v.hi; sg[2 * n + i] = t.z.hi;
+      sg[3 * n + i] = t.qu.hi; sg[4 * n + i] = t.qv.hi; sg[5 * n + i] = t.pz.hi;
+      sg[6 * n + i] = t.u.lo; sg[7 * n + i] = t.v.lo; sg[8 * n + i] = t.z.lo;
+      sg[9 * n + i] = t.qu.lo; sg[10 * n + i] = t.qv.lo; sg[11 * n + i] = t.pz.lo;
     }
     float lu = a.lamf[i], lv = a.lamf[n + i], lz = a.lamf[2 * n + i];
     float lqu = a.lamf[3 * n + i], lqv = a.lamf[4 * n + i], lpz = a.lamf[5 * n + i];
@@ -173,26 +187,16 @@ __global__ void __launch_bounds__(128) k_adjoint_fp32c(AdjArgs a, Tab32 tb) {
       t.qu = {sg[3 * n + i], sg[9 * n + i]};
       t.qv = {sg[4 * n + i], sg[10 * n + i]};
       t.pz = {sg[5 * n + i], sg[11 * n + i]};
-      Pair xk[M][3];
-      float qd[M + 1][3];
-      qd[0][0] = t.qu.hi; qd[0][1] = t.qv.hi; qd[0][2] = t.pz.hi;
-      drift32<false>(t, a.cf.sig_hi[0], a.cf.sig_lo[0]);
-#pragma unroll
-      for (int k = 0; k < M; ++k) {
-        xk[k][0] = t.u; xk[k][1] = t.v; xk[k][2] = t.z;
-        kick32<false>(t, a.cf.k2f[k], a.cf.k4f[k], ssc, tb);
-        qd[k + 1][0] = t.qu.hi; qd[k + 1][1] = t.qv.hi; qd[k + 1][2] = t.pz.hi;
-        drift32<false>(t, a.cf.sig_hi[k + 1], a.cf.sig_lo[k + 1]);
-      }
 #pragma unroll
       for (int k = M; k >= 0; --k) {
-        acc_pair(gh, a.cdf[k] * fmaf(lu, qd[k][0], fmaf(lv, qd[k][1], lz * qd[k][2])));
+        acc_pair(gh, a.cdf[k] * fmaf(lu, t.qu.hi, fmaf(lv, t.qv.hi, lz * t.pz.hi)));
         lqu = fmaf(a.cf.sig_hi[k], lu, lqu);
         lqv = fmaf(a.cf.sig_hi[k], lv, lqv);
         lpz = fmaf(a.cf.sig_hi[k], lz, lpz);
+        drift32<false>(t, -a.cf.sig_hi[k], -a.cf.sig_lo[k]);
         if (k > 0)
-          adj_kick32(lu, lv, lz, lqu, lqv, lpz, xk[k - 1][0], xk[k - 1][1], xk[k - 1][2], a.cf.k2f[k - 1],
-                     a.cf.k4f[k - 1], a.chf[k - 1], a.cef[k - 1], gh, ge, ssc, tb);
+          adj_kick32(lu, lv, lz, lqu, lqv, lpz, t, a.cf.k2f[k - 1], a.cf.k4f[k - 1], a.chf[k - 1], a.cef[k - 1], gh,
+                     ge, ssc, tb);
       }
     }
     a.lamf[i] = lu; a.lamf[n + i] = lv; a.lamf[2 * n + i] = lz;
@@ -275,14 +279,30 @@ cudaError_t launch64(const AdjArgs& a, int grid, cudaStream_t st) {
   auto k = k_adjoint_fp64<M>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTabSmemBytes);
   if (e != cudaSuccess) return e;
-  k<<<grid, 128, kTabSmemBytes, st>>>(a);
+  k<<<grid, 256, kTabSmemBytes, st>>>(a);
   return cudaGetLastError();
 }
 
 template <int M>
+int occ64() {
+  auto k = k_adjoint_fp64<M>;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTabSmemBytes) != cudaSuccess) return 1;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, 256, kTabSmemBytes) != cudaSuccess) return 1;
+  return nb > 0 ? nb : 1;
+}
+
+template <int M>
 cudaError_t launch32(const AdjArgs& a, const Tab32& tb, int grid, cudaStream_t st) {
-  k_adjoint_fp32c<M><<<grid, 128, (size_t)(tb.jmax + 1) * sizeof(float2), st>>>(a, tb);
+  k_adjoint_fp32c<M><<<grid, 256, (size_t)(tb.jmax + 1) * sizeof(float2), st>>>(a, tb);
   return cudaGetLastError();
+}
+
+template <int M>
+int occ32(size_t smem) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adjoint_fp32c<M>, 256, smem) != cudaSuccess) return 1;
+  return nb > 0 ? nb : 1;
 }
 
 }  // namespace
@@ -306,6 +326,17 @@ cudaError_t launch_adjoint_segment(const AdjArgs& a, int scheme, bool fp32c, int
     }
   }
   return cudaErrorInvalidValue;
+}
+
+int adjoint_blocks_per_sm(int scheme, bool fp32c) {
+  if (fp32c) {
+    Tab32 tb;
+    fp32_tab(&tb);
+    const size_t smem = (size_t)(tb.jmax + 1) * sizeof(float2);
+    return scheme == ARNOLD_SCHEME_YOSHIDA6A ? occ32<7>(smem)
+                                             : (scheme == ARNOLD_SCHEME_TRIPLEJUMP6 ? occ32<9>(smem) : occ32<1>(smem));
+  }
+  return scheme == ARNOLD_SCHEME_YOSHIDA6A ? occ64<7>() : (scheme == ARNOLD_SCHEME_TRIPLEJUMP6 ? occ64<9>() : occ64<1>());
 }
 
 cudaError_t launch_adj_init(long long n, const double* dx, const double* dp, double* lam, float* lamf, double* gh,

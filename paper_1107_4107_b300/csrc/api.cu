@@ -106,7 +106,7 @@ int params_ok(const arnold_params* p) {
   if (p->tangent != 0 && p->tangent != 1) return 0;
   if (p->renorm_every < 1 || p->window < 0) return 0;
   if (!(p->chaos_kappa > 0.0)) return 0;
-  if (p->block_size != 0 && (p->block_size < 32 || p->block_size > 512 || p->block_size % 32)) return 0;
+  if (p->block_size != 0 && (p->block_size < 32 || p->block_size > 256 || p->block_size % 32)) return 0;
   if (p->launch_steps < 0) return 0;
   return 1;
 }
@@ -676,8 +676,8 @@ int arnold_grad(arnold_ctx* c, const double* dL_dx, const double* dL_dp, double*
     a.cd[k] = 0.5 * (left + right);
     a.cdf[k] = (float)a.cd[k];
   }
-  long long g = (c->n + 127) / 128;
-  const long long cap = (long long)c->sms * 2;
+  long long g = (c->n + 255) / 256;
+  const long long cap = (long long)c->sms * adjoint_blocks_per_sm(c->prm.scheme, f32);
   if (g > cap) g = cap;
   for (long long k = c->adj_K - 1; k >= 0; --k) {
     a.k = (int)k;

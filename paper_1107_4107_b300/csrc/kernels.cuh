@@ -66,6 +66,7 @@ struct AdjArgs {
 };
 
 cudaError_t launch_adjoint_segment(const AdjArgs& a, int scheme, bool fp32c, int grid, cudaStream_t st);
+int adjoint_blocks_per_sm(int scheme, bool fp32c);   // with 256-thread blocks
 cudaError_t launch_adj_init(long long n, const double* dx, const double* dp, double* lam, float* lamf, double* gh,
                             double* ge, int grid, cudaStream_t st);
 cudaError_t launch_adj_finish(long long n, const double* lam, const float* lamf, double* gx, double* gp, int grid,
