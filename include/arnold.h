@@ -265,6 +265,21 @@ int arnold_batch_sync(arnold_batch* b);
 int64_t arnold_batch_launch_count(const arnold_batch* b);
 void arnold_batch_destroy(arnold_batch* b);
 
+/* ---- checkpoint / resume ----------------------------------------------------
+ * The complete per-trajectory state (phase-space state, tangent, laps, window
+ * references, log sums, energy references and maxima, V) plus the step
+ * counter, so that a run resumed from a checkpoint continues bit for bit as
+ * if uninterrupted (the paper's 24 h runs, Sec. IV, motivate it).  Layout: a
+ * 64-byte header (magic "ARNOLDC1", precision, tangent, n, steps, scheme,
+ * eps, h) followed by the device arrays.  The buffer is host memory owned by
+ * the caller. */
+int arnold_checkpoint_size(const arnold_ctx* ctx, size_t* bytes);
+/* Synchronises.  Errors: EINVAL (NULL, bytes too small), ECUDA. */
+int arnold_checkpoint_save(arnold_ctx* ctx, void* host_buf, size_t bytes);
+/* The context must have the same n, precision, tangent, scheme, eps and h.
+ * Errors: EINVAL (mismatch, bad magic, size), ECUDA. */
+int arnold_checkpoint_load(arnold_ctx* ctx, const void* host_buf, size_t bytes);
+
 /* Synchronise the context's stream; returns the first pending error. */
 int arnold_sync(arnold_ctx* ctx);
 

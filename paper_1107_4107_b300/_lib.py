@@ -80,6 +80,9 @@ SIGNATURES = {
     "arnold_batch_sync": (ctypes.c_int, [vp]),
     "arnold_batch_launch_count": (i64, [vp]),
     "arnold_batch_destroy": (None, [vp]),
+    "arnold_checkpoint_size": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "arnold_checkpoint_save": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
+    "arnold_checkpoint_load": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
     "arnold_sync": (ctypes.c_int, [vp]),
     "arnold_launch_count": (i64, [vp]),
     "arnold_strerror": (ctypes.c_char_p, [ctypes.c_int]),

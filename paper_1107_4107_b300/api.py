@@ -147,6 +147,27 @@ class ArnoldEnsemble:
               "arnold_stats_arrays")
         return stats_dict(s)
 
+    # -- checkpoint / resume --
+    def checkpoint(self) -> bytes:
+        """Complete state as bytes (resume continues bit for bit)."""
+        size = ctypes.c_size_t()
+        check(_lib.lib().arnold_checkpoint_size(self._h, ctypes.byref(size)), "arnold_checkpoint_size")
+        buf = ctypes.create_string_buffer(size.value)
+        check(_lib.lib().arnold_checkpoint_save(self._h, buf, size.value), "arnold_checkpoint_save")
+        return buf.raw
+
+    def restore(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        check(_lib.lib().arnold_checkpoint_load(self._h, buf, len(blob)), "arnold_checkpoint_load")
+
+    def save(self, path: str):
+        with open(path, "wb") as f:
+            f.write(self.checkpoint())
+
+    def load(self, path: str):
+        with open(path, "rb") as f:
+            self.restore(f.read())
+
     # -- differentiation --
     def forward_ckpt(self, n_steps: int, ckpt_every: int = 0):
         """Advance n_steps keeping sqrt(N) checkpoints for grad()."""

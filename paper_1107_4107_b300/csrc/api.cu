@@ -703,6 +703,100 @@ int arnold_grad(arnold_ctx* c, const double* dL_dx, const double* dL_dp, double*
   return ARNOLD_OK;
 }
 
+struct CkptHeader {
+  char magic[8];
+  int32_t precision, tangent;
+  int64_t n, steps;
+  int32_t scheme, pad;
+  double eps, h;
+  int64_t reserved;
+};
+static_assert(sizeof(CkptHeader) == 64, "checkpoint header is 64 bytes");
+
+// (device pointer, bytes) of every array that makes up the state.
+static int ckpt_arrays(const arnold_ctx* c, void** ptrs, size_t* sizes) {
+  const size_t n = (size_t)c->n;
+  int k = 0;
+  auto add = [&](void* p, size_t b) {
+    if (p) { ptrs[k] = p; sizes[k] = b; ++k; }
+  };
+  add(c->s.st, 48 * n);
+  add(c->s.tg, 48 * n);
+  add(c->f.hi, 24 * n);
+  add(c->f.lo, 24 * n);
+  add(c->f.tg, 24 * n);
+  add(c->s.lap, 12 * n);
+  add(c->s.lapref, 12 * n);
+  add(c->s.ref, 24 * n);
+  add(c->s.logsum, 8 * n);
+  add(c->s.demax, 8 * n);
+  add(c->s.e0, 8 * n);
+  add(c->s.V, 24 * n);
+  return k;
+}
+
+int arnold_checkpoint_size(const arnold_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return ARNOLD_EINVAL;
+  void* p[16];
+  size_t sz[16];
+  const int k = ckpt_arrays(c, p, sz);
+  size_t total = sizeof(CkptHeader);
+  for (int i = 0; i < k; ++i) total += sz[i];
+  *bytes = total;
+  return ARNOLD_OK;
+}
+
+int arnold_checkpoint_save(arnold_ctx* c, void* buf, size_t bytes) {
+  size_t need = 0;
+  if (!c || !buf || arnold_checkpoint_size(c, &need) || bytes < need) return ARNOLD_EINVAL;
+  ACHECK(cudaSetDevice(c->device));
+  CkptHeader hd;
+  memset(&hd, 0, sizeof hd);
+  memcpy(hd.magic, "ARNOLDC1", 8);
+  hd.precision = c->prm.precision;
+  hd.tangent = c->prm.tangent;
+  hd.n = c->n;
+  hd.steps = c->steps;
+  hd.scheme = c->prm.scheme;
+  hd.eps = c->prm.eps;
+  hd.h = c->prm.h;
+  memcpy(buf, &hd, sizeof hd);
+  void* p[16];
+  size_t sz[16];
+  const int k = ckpt_arrays(c, p, sz);
+  char* dst = (char*)buf + sizeof hd;
+  for (int i = 0; i < k; ++i) {
+    ACHECK(cudaMemcpyAsync(dst, p[i], sz[i], cudaMemcpyDeviceToHost, c->stream));
+    dst += sz[i];
+  }
+  ACHECK(cudaStreamSynchronize(c->stream));
+  return ARNOLD_OK;
+}
+
+int arnold_checkpoint_load(arnold_ctx* c, const void* buf, size_t bytes) {
+  size_t need = 0;
+  if (!c || !buf || arnold_checkpoint_size(c, &need) || bytes < need) return ARNOLD_EINVAL;
+  CkptHeader hd;
+  memcpy(&hd, buf, sizeof hd);
+  if (memcmp(hd.magic, "ARNOLDC1", 8) || hd.precision != c->prm.precision || hd.tangent != c->prm.tangent ||
+      hd.n != c->n || hd.scheme != c->prm.scheme || hd.eps != c->prm.eps || hd.h != c->prm.h || hd.steps < 0)
+    return ARNOLD_EINVAL;
+  ACHECK(cudaSetDevice(c->device));
+  void* p[16];
+  size_t sz[16];
+  const int k = ckpt_arrays(c, p, sz);
+  const char* src = (const char*)buf + sizeof hd;
+  for (int i = 0; i < k; ++i) {
+    ACHECK(cudaMemcpyAsync(p[i], src, sz[i], cudaMemcpyHostToDevice, c->stream));
+    src += sz[i];
+  }
+  ACHECK(cudaMemsetAsync(c->flags, 0, sizeof(int), c->stream));
+  ACHECK(cudaStreamSynchronize(c->stream));
+  c->steps = hd.steps;
+  c->adj_valid = 0;
+  return ARNOLD_OK;
+}
+
 int arnold_sync(arnold_ctx* c) {
   if (!c) return ARNOLD_EINVAL;
   if (fault_is("timeout")) return ARNOLD_ETIMEOUT;

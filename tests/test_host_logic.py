@@ -1,0 +1,118 @@
+"""Host-side logic on CPU: parameter plumbing, batched-scan set generator, shard
+layout, statistics merging, and the two-rank merge over torch.distributed (gloo)."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1107_4107_b300 import params, shard
+
+
+def test_parameter_conversions():
+    assert params.eps_eff(400.0) == 0.005
+    assert abs(params.energy_for(params.eps_eff(15.0)) - 15.0) < 1e-12
+    h = params.paper_h()
+    K = params.kick_strength(1.0, h)
+    assert abs(params.h_for(K) - h) < 1e-15
+    # chain rule h = sqrt(K / eps): compare with finite differences of a smooth f(h, eps)
+    f = lambda hh, ee: math.sin(hh * 3.0) + ee ** 2 * hh          # noqa: E731
+    g_h = 3.0 * math.cos(h * 3.0) + 1.0 ** 2
+    g_e = 2.0 * 1.0 * h
+    dK, de = params.grads_K_eps(g_h, g_e, h, 1.0)
+    d = 1e-7
+    fK = lambda KK, ee: f(math.sqrt(KK / ee), ee)                   # noqa: E731
+    assert abs((fK(K + d, 1.0) - fK(K - d, 1.0)) / (2 * d) - dK) < 1e-6 * abs(dK)
+    assert abs((fK(K, 1.0 + d) - fK(K, 1.0 - d)) / (2 * d) - de) < 1e-6 * max(1, abs(de))
+
+
+def test_batch_sets_generator():
+    s = params.batch_sets()
+    assert len(s) == 64
+    ee = sorted({q["eps_eff"] for q in s})
+    KK = sorted({q["K"] for q in s})
+    assert len(ee) == 8 and len(KK) == 8
+    assert abs(ee[0] - 1e-5) < 1e-18 and abs(ee[-1] - 0.1) < 1e-15
+    assert abs(KK[0] - (0.005 * 2 * math.pi) ** 2) < 1e-15 and abs(KK[-1] - (0.02 * 2 * math.pi) ** 2) < 1e-15
+    for q in s:
+        assert 1e3 * 0.8 <= q["G"] ** 2 <= 1e6 * 1.01 and 1e4 <= q["n_steps"] <= 1e6
+        assert abs(q["E"] - 2.0 / q["eps_eff"]) < 1e-9 * q["E"]
+        assert abs(q["h"] ** 2 - q["K"]) < 1e-15
+    assert s == params.batch_sets()             # seeded, reproducible
+
+
+@pytest.mark.parametrize("G,world", [(2048, 1), (2048, 3), (17, 4), (5, 5)])
+def test_row_bands_partition_the_grid(G, world):
+    bands = [shard.row_band(G, r, world) for r in range(world)]
+    assert bands[0][0] == 0
+    for (r0, n0), (r1, _) in zip(bands, bands[1:]):
+        assert r0 + n0 == r1
+    assert sum(n for _, n in bands) == G
+    assert max(n for _, n in bands) - min(n for _, n in bands) <= 1
+
+
+def _synthetic(n, seed):
+    rng = np.random.default_rng(seed)
+    chi = 10.0 ** rng.uniform(-9, 2, n)
+    dE = rng.uniform(0, 1e-3, n)
+    P = rng.normal(size=(3, n)) * [[1.0], [2.0], [3.0]] + [[5.0], [0.0], [-2.0]]
+    return chi, dE, P
+
+
+def test_merge_stats_equals_unsharded():
+    chi, dE, P = _synthetic(10001, 1)
+    t = 628.3
+    whole = oracle.stats(chi, dE, P, t)
+    cuts = [0, 17, 5000, 5001, 10001]
+    parts = []
+    for a, b in zip(cuts, cuts[1:]):
+        p = oracle.stats(chi[a:b], dE[a:b], P[:, a:b], t)
+        p["n"] = b - a
+        parts.append(p)
+    m = shard.merge_stats(parts)
+    assert np.array_equal(m["hist"], whole["hist"])
+    for k in ("under", "over", "chaotic"):
+        assert m[k] == whole[k]
+    assert m["dE_max"] == whole["dE_max"]
+    np.testing.assert_allclose(m["p_mean"], whole["p_mean"], rtol=1e-12)
+    np.testing.assert_allclose(m["p_var"], whole["p_var"], rtol=1e-12)
+
+
+def _rank_main(rank, world, port, n, out_path):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    chi, dE, P = _synthetic(n, 7)
+    r0, rows = shard.row_band(n, rank, world)
+    part = oracle.stats(chi[r0:r0 + rows], dE[r0:r0 + rows], P[:, r0:r0 + rows], 100.0)
+    part["n"] = rows
+    merged = shard.gather_stats(part)
+    if rank == 0:
+        np.save(out_path, np.concatenate([merged["hist"], [merged["under"], merged["over"], merged["chaotic"],
+                                                            merged["n"]], merged["p_mean"], merged["p_var"]]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_gloo_merge(tmp_path):
+    """World size 2 over gloo on CPU: each rank reduces its band, the merged
+    statistics equal those of the whole ensemble."""
+    import socket
+
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    n = 4001
+    out = str(tmp_path / "merged.npy")
+    mp.start_processes(_rank_main, args=(2, port, n, out), nprocs=2, join=True, start_method="spawn")
+    got = np.load(out)
+    chi, dE, P = _synthetic(n, 7)
+    whole = oracle.stats(chi, dE, P, 100.0)
+    nb = len(whole["hist"])
+    assert np.array_equal(got[:nb], whole["hist"])
+    assert list(got[nb:nb + 4]) == [whole["under"], whole["over"], whole["chaotic"], n]
+    np.testing.assert_allclose(got[nb + 4:nb + 7], whole["p_mean"], rtol=1e-12)
+    np.testing.assert_allclose(got[nb + 7:nb + 10], whole["p_var"], rtol=1e-12)
