@@ -73,6 +73,7 @@ extern "C" {
 #define ARNOLD_IND_DX       7  /* [3][n] f64: unwrapped X(now) - X(window start) (window 0: since start)  */
 #define ARNOLD_IND_TANGENT  8  /* [6][n] f64: (dx, dy, dz, dp_x, dp_y, dp_z), as renormalised             */
 #define ARNOLD_IND_LOGSUM   9  /* [n] f64: sum of ln|w| taken at renormalisations                        */
+#define ARNOLD_IND_LEFT    10  /* [n] u8: 1 if the momentum direction left the tracked patch (area filter) */
 
 /* ---- parameters ------------------------------------------------------------ */
 typedef struct arnold_params {
@@ -126,6 +127,36 @@ int arnold_set_state(arnold_ctx* ctx, const double* x, const double* p, const do
  * Errors: EINVAL (E <= 2|eps|, size mismatch), ECUDA. */
 int arnold_init_grid(arnold_ctx* ctx, int64_t G, int64_t row0, double E, uint64_t seed,
                      double* raw_out);
+
+/* Initial conditions on the energy shell (the ensembles of Sec. IV, uniform
+ * over the sphere S or a patch of it, and the Gaussian cloud of Fig. 4): x is
+ * [3][n] angles; with mode ARNOLD_SHELL_DIRECTION p holds unit directions and
+ * P = sqrt(2 (E - eps Hp(X))) p; with ARNOLD_SHELL_PZ p holds (p_x, p_y, -)
+ * and p_z = +sqrt(2 (E - eps Hp) - p_x^2 - p_y^2).  Otherwise as
+ * arnold_set_state (tangent (1,...,1)/sqrt 6).  A negative radicand gives NaN
+ * momenta, reported as ENONFINITE by the next sync.  Errors: EINVAL, ECUDA. */
+#define ARNOLD_SHELL_DIRECTION 1
+#define ARNOLD_SHELL_PZ        2
+int arnold_set_state_shell(arnold_ctx* ctx, const double* x, const double* p, int mode, double E,
+                           int ptr_kind);
+
+/* Area tracking (Sec. IV, Fig. 3 zooms: trajectories that leave the scanned
+ * area are dropped): from now on, every renorm_every steps, a trajectory whose
+ * momentum direction (cos theta = p_z/|P|, phi = atan2(p_y, p_x) in [0, 2pi))
+ * is outside [cos_lo, cos_hi] x [phi_lo, phi_hi] is flagged (ARNOLD_IND_LEFT).
+ * Flags reset at set_state / init_grid / this call.  Errors: EINVAL, ENOMEM. */
+int arnold_track_patch(arnold_ctx* ctx, double cos_lo, double cos_hi, double phi_lo, double phi_hi);
+
+/* Density of V on the momentum sphere (F of Sec. IV, Figs. 2-4): counts of the
+ * direction of V (ARNOLD_IND_V) in n_cos x n_phi equal-width cells of
+ * cos theta in [cos_lo, cos_hi] and phi in [phi_lo, phi_hi]; directions
+ * outside are not counted, nor (filtered != 0) flagged trajectories.  counts:
+ * [n_cos][n_phi] u64; accumulate != 0 adds to its contents (time-averaged F
+ * over several windows), else it is overwritten.  Host counts synchronise.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int arnold_velocity_histogram(arnold_ctx* ctx, int n_cos, int n_phi, double cos_lo, double cos_hi,
+                              double phi_lo, double phi_hi, int filtered, uint64_t* counts, int ptr_kind,
+                              int accumulate);
 
 /* Advance every trajectory n_steps >= 0 composite steps (asynchronous).
  * Work is split into launches of at most launch_steps steps; the result does

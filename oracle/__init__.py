@@ -67,6 +67,11 @@ def lib():
         L.oracle_energy.argtypes = [ctypes.c_double, ctypes.c_int64, dp, dp, dp]
         L.oracle_pz_from_energy.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int64, dp, dp]
         L.oracle_pz_from_energy.restype = ctypes.c_int64
+        L.oracle_momenta_on_shell.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int64, dp, dp, dp]
+        L.oracle_momenta_on_shell.restype = ctypes.c_int64
+        L.oracle_track.argtypes = [ctypes.POINTER(_Params), ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, dp, dp, dp,
+                                   ctypes.POINTER(ctypes.c_uint8)]
+        L.oracle_track.restype = ctypes.c_int
         L.oracle_jacobian.argtypes = [ctypes.POINTER(_Params), ctypes.c_int64, ctypes.c_int64, dp, dp, dp, dp, dp]
         L.oracle_jacobian.restype = ctypes.c_int
         L.oracle_scheme_weights.argtypes = [ctypes.c_int, dp]
@@ -144,6 +149,53 @@ def pz_from_energy(E: float, eps: float, X: np.ndarray, P: np.ndarray) -> np.nda
     P = np.array(P, dtype=np.float64, order="C", copy=True)
     lib().oracle_pz_from_energy(E, eps, X.shape[1], _ptr(X), _ptr(P))
     return P
+
+
+def momenta_on_shell(E: float, eps: float, X: np.ndarray, nhat: np.ndarray) -> np.ndarray:
+    """P = sqrt(2 (E - eps Hp(X))) nhat (Sec. IV: ensembles on the sphere S)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    nhat = np.ascontiguousarray(nhat, dtype=np.float64)
+    P = np.zeros_like(nhat)
+    lib().oracle_momenta_on_shell(E, eps, X.shape[1], _ptr(X), _ptr(nhat), _ptr(P))
+    return P
+
+
+def track_patch(params: Params, X, P, n_steps: int, patch, step0: int = 0):
+    """Area tracking (Sec. IV): returns (X_N, P_N, left[n] uint8) with left = 1 for
+    trajectories whose momentum direction left the patch (cos_lo, cos_hi,
+    phi_lo, phi_hi) at any sample (every renorm_every steps)."""
+    X = np.array(X, dtype=np.float64, order="C", copy=True)
+    P = np.array(P, dtype=np.float64, order="C", copy=True)
+    n = X.shape[1]
+    left = np.zeros(n, dtype=np.uint8)
+    pa = np.ascontiguousarray(patch, dtype=np.float64)
+    rc = lib().oracle_track(ctypes.byref(params.c()), n, step0, n_steps, _ptr(X), _ptr(P), _ptr(pa),
+                            left.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+    if rc != 0:
+        raise ValueError("oracle_track rejected its arguments")
+    return X, P, left
+
+
+def velocity_histogram(V: np.ndarray, n_cos: int, n_phi: int, patch=(-1.0, 1.0, 0.0, TWO_PI), keep=None) -> np.ndarray:
+    """Counts of the direction of V (Sec. IV: the density F of V projected on the
+    sphere S) in n_cos x n_phi cells of equal width in cos theta and phi over
+    the patch; directions outside the patch, and trajectories with keep = 0,
+    are not counted."""
+    V = np.asarray(V, dtype=np.float64)
+    m = np.sqrt(V[0] ** 2 + V[1] ** 2 + V[2] ** 2)
+    c = V[2] / m
+    phi = np.arctan2(V[1], V[0])
+    phi = np.where(phi < 0.0, phi + TWO_PI, phi)
+    counts = np.zeros((n_cos, n_phi), dtype=np.int64)
+    for i in range(V.shape[1]):
+        if keep is not None and not keep[i]:
+            continue
+        if not (patch[0] <= c[i] <= patch[1] and patch[2] <= phi[i] <= patch[3]):
+            continue
+        a = min(int((c[i] - patch[0]) / (patch[1] - patch[0]) * n_cos), n_cos - 1)
+        b = min(int((phi[i] - patch[2]) / (patch[3] - patch[2]) * n_phi), n_phi - 1)
+        counts[a, b] += 1
+    return counts
 
 
 class State:

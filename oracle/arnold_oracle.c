@@ -250,6 +250,55 @@ int oracle_run(const oracle_params* prm, int64_t n, int64_t step0, int64_t n_ste
   return 0;
 }
 
+/*
+ * Momenta on the energy shell along given unit directions (the ensembles of
+ * Sec. IV, uniform over the sphere S): |P| = sqrt(2 (E - eps Hp(X))),
+ * P = |P| nhat.  Returns the number of points with a negative radicand (P = NaN).
+ */
+int64_t oracle_momenta_on_shell(double E, double eps, int64_t n, const double* X, const double* nhat, double* P) {
+  int64_t bad = 0;
+  for (int64_t i = 0; i < n; i++) {
+    double r = 2.0 * (E - eps * oracle_hp(X[i], X[n + i], X[2 * n + i]));
+    double m = r >= 0.0 ? sqrt(r) : NAN;
+    if (!(r >= 0.0)) bad++;
+    for (int a = 0; a < 3; a++) P[a * n + i] = m * nhat[a * n + i];
+  }
+  return bad;
+}
+
+/*
+ * Area tracking (Sec. IV, Fig. 3 zooms: only trajectories that stay within the
+ * scanned area for the whole observation time are kept).  Sampled every R
+ * steps: the momentum direction (cos theta = p_z / |P|, phi = atan2(p_y, p_x)
+ * in [0, 2pi)) must stay inside [cos_lo, cos_hi] x [phi_lo, phi_hi];
+ * left[i] becomes 1 the first time it does not.
+ */
+static int inside_patch(const double P[3], const double* patch) {
+  double m = sqrt(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
+  double c = P[2] / m;
+  double phi = atan2(P[1], P[0]);
+  if (phi < 0.0) phi += ORACLE_TWO_PI;
+  return c >= patch[0] && c <= patch[1] && phi >= patch[2] && phi <= patch[3];
+}
+
+int oracle_track(const oracle_params* prm, int64_t n, int64_t step0, int64_t n_steps, double* X, double* P,
+                 const double* patch, uint8_t* left) {
+  double wts[9];
+  int m = oracle_scheme_weights(prm->scheme, wts);
+  if (m < 0 || prm->renorm_every < 1) return -1;
+  for (int64_t i = 0; i < n; i++) {
+    traj t;
+    memset(&t, 0, sizeof t);
+    for (int a = 0; a < 3; a++) { t.X[a] = X[a * n + i]; t.P[a] = P[a * n + i]; }
+    for (int64_t s = 0; s < n_steps; s++) {
+      composite_step(&t, prm, wts, m, 0);
+      if ((step0 + s + 1) % prm->renorm_every == 0 && !inside_patch(t.P, patch)) left[i] = 1;
+    }
+    for (int a = 0; a < 3; a++) { X[a * n + i] = t.X[a]; P[a * n + i] = t.P[a]; }
+  }
+  return 0;
+}
+
 /* Energy (Eq. 1) of n SoA points. */
 void oracle_energy(double eps, int64_t n, const double* X, const double* P, double* E) {
   for (int64_t i = 0; i < n; i++) {

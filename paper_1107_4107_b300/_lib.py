@@ -15,8 +15,11 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, EUNSUPPORTED, ESTATE = 0, -1, -
 SCHEMES = {"yoshida6a": 0, "triplejump6": 1, "leapfrog2": 2}
 PRECISIONS = {"fp64": 0, "fp32c": 1}
 HOST, DEVICE = 0, 1
-IND = {"chi": 0, "V": 1, "dE": 2, "dE_max": 3, "class": 4, "X": 5, "P": 6, "dX": 7, "tangent": 8, "logsum": 9}
-IND_SHAPE = {"chi": 1, "V": 3, "dE": 1, "dE_max": 1, "class": 1, "X": 3, "P": 3, "dX": 3, "tangent": 6, "logsum": 1}
+IND = {"chi": 0, "V": 1, "dE": 2, "dE_max": 3, "class": 4, "X": 5, "P": 6, "dX": 7, "tangent": 8, "logsum": 9,
+       "left": 10}
+IND_SHAPE = {"chi": 1, "V": 3, "dE": 1, "dE_max": 1, "class": 1, "X": 3, "P": 3, "dX": 3, "tangent": 6, "logsum": 1,
+             "left": 1}
+SHELL_DIRECTION, SHELL_PZ = 1, 2
 HIST_BINS = 200
 NOALLOC_MAX_N = 1 << 40
 
@@ -60,6 +63,10 @@ SIGNATURES = {
     "arnold_set_state": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_int]),
     "arnold_init_grid": (ctypes.c_int, [vp, i64, i64, ctypes.c_double, ctypes.c_uint64, vp]),
     "arnold_iterate": (ctypes.c_int, [vp, i64]),
+    "arnold_set_state_shell": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_int]),
+    "arnold_track_patch": (ctypes.c_int, [vp] + [ctypes.c_double] * 4),
+    "arnold_velocity_histogram": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4 +
+                                  [ctypes.c_int, vp, ctypes.c_int, ctypes.c_int]),
     "arnold_steps_done": (i64, [vp]),
     "arnold_indicator": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int]),
     "arnold_stats_compute": (ctypes.c_int, [vp, ctypes.POINTER(Stats)]),

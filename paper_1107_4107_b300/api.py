@@ -102,6 +102,43 @@ class ArnoldEnsemble:
         pr, _ = _ptr_kind(raw_out)
         check(_lib.lib().arnold_init_grid(self._h, G, row0, E, seed, pr), "arnold_init_grid")
 
+    def set_state_shell(self, X, Pdir, mode: int, E: float):
+        """Fixed-energy initial momenta (Sec. IV): mode 1 scales unit directions
+        Pdir to the shell, mode 2 takes (p_x, p_y) and sets p_z from the energy."""
+        px, kx = _ptr_kind(X)
+        pp, kp = _ptr_kind(Pdir)
+        if kx != kp:
+            raise ValueError("X and P must both be host or both device")
+        check(_lib.lib().arnold_set_state_shell(self._h, px, pp, int(mode), float(E), kx), "arnold_set_state_shell")
+
+    def init_sphere(self, E: float, seed: int = 0, cos_range=(-1.0, 1.0), phi_range=(0.0, 2 * math.pi)):
+        """Ensemble uniform over (a patch of) the momentum sphere S and over the
+        torus (Sec. IV, Figs. 2-3); directions drawn on the host (inputs module)."""
+        from .inputs import sphere_directions
+        X, nhat = sphere_directions(self.n, seed, cos_range, phi_range)
+        self.set_state_shell(X, nhat, _lib.SHELL_DIRECTION, E)
+
+    def init_gaussian(self, E: float, center, sigma: float = 0.01, seed: int = 0):
+        """Gaussian cloud in (p_x, p_y) about `center`, p_z from the energy (Fig. 4)."""
+        from .inputs import gaussian_velocities
+        X, Pxy = gaussian_velocities(self.n, center, sigma, seed)
+        P = np.zeros((3, self.n))
+        P[:2] = Pxy
+        self.set_state_shell(X, P, _lib.SHELL_PZ, E)
+
+    def track_patch(self, cos_lo: float, cos_hi: float, phi_lo: float, phi_hi: float):
+        check(_lib.lib().arnold_track_patch(self._h, cos_lo, cos_hi, phi_lo, phi_hi), "arnold_track_patch")
+
+    def velocity_histogram(self, n_cos: int, n_phi: int, patch=(-1.0, 1.0, 0.0, 2 * math.pi), filtered: bool = False,
+                           out=None, accumulate: bool = False):
+        """Counts of the direction of V on the momentum sphere (F of Sec. IV)."""
+        if out is None:
+            out = np.zeros((n_cos, n_phi), dtype=np.uint64)
+        po, ko = _ptr_kind(out)
+        check(_lib.lib().arnold_velocity_histogram(self._h, n_cos, n_phi, *[float(v) for v in patch], int(filtered), po,
+                                                   ko, int(accumulate)), "arnold_velocity_histogram")
+        return out
+
     def iterate(self, n_steps: int):
         check(_lib.lib().arnold_iterate(self._h, int(n_steps)), "arnold_iterate")
 
@@ -126,7 +163,7 @@ class ArnoldEnsemble:
         tensor) or a new numpy array."""
         rows = _lib.IND_SHAPE[kind]
         if out is None:
-            dtype = np.uint8 if kind == "class" else np.float64
+            dtype = np.uint8 if kind in ("class", "left") else np.float64
             out = np.empty((rows, self.n) if rows > 1 else (self.n,), dtype=dtype)
         po, ko = _ptr_kind(out)
         check(_lib.lib().arnold_indicator(self._h, _lib.IND[kind], po, ko), f"arnold_indicator({kind})")

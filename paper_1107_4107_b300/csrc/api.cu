@@ -76,6 +76,8 @@ struct arnold_ctx {
   double* sum_part = nullptr;  // [2 * stats_grid + 2]
   int adj_valid = 0;
   long long adj_N = 0, adj_C = 0, adj_K = 0;
+  unsigned long long* vhist = nullptr;   // device counts for host-side histograms
+  size_t vhist_cells = 0;
 };
 
 namespace {
@@ -205,7 +207,8 @@ cudaError_t dalloc(T** p, size_t count) {
 void free_all(arnold_ctx* c) {
   void* ptrs[] = {c->s.st, c->s.tg, c->s.lap, c->s.lapref, c->s.ref, c->s.logsum, c->s.demax, c->s.e0, c->s.V,
                   c->f.hi, c->f.lo, c->f.tg, c->sc, c->th, c->scf, c->flags, c->partials, c->stats_out,
-                  c->scratch, c->scratch2, c->ck, c->seg, c->lam, c->lamf, c->gh, c->ge, c->sum_part};
+                  c->scratch, c->scratch2, c->ck, c->seg, c->lam, c->lamf, c->gh, c->ge, c->sum_part, c->s.left,
+                  c->vhist};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -269,7 +272,7 @@ int read_indicator(arnold_ctx* c, int kind, void* dst) {
 size_t indicator_bytes(int kind, long long n) {
   switch (kind) {
     case ARNOLD_IND_CHI: case ARNOLD_IND_DE: case ARNOLD_IND_DE_MAX: case ARNOLD_IND_LOGSUM: return 8 * (size_t)n;
-    case ARNOLD_IND_CLASS: return (size_t)n;
+    case ARNOLD_IND_CLASS: case ARNOLD_IND_LEFT: return (size_t)n;
     case ARNOLD_IND_V: case ARNOLD_IND_X: case ARNOLD_IND_P: case ARNOLD_IND_DX: return 24 * (size_t)n;
     case ARNOLD_IND_TANGENT: return 48 * (size_t)n;
   }
@@ -390,10 +393,13 @@ void arnold_destroy(arnold_ctx* c) {
   delete c;
 }
 
-int arnold_set_state(arnold_ctx* c, const double* x, const double* p, const double* w, int ptr_kind) {
+static int set_state_mode(arnold_ctx* c, const double* x, const double* p, const double* w, int ptr_kind, int mode,
+                          double E) {
   if (!c || !x || !p || (ptr_kind != ARNOLD_HOST && ptr_kind != ARNOLD_DEVICE)) return ARNOLD_EINVAL;
   ACHECK(cudaSetDevice(c->device));
   InitArgs a = init_args(c);
+  a.shell_mode = mode;
+  a.E = E;
   const size_t n = (size_t)c->n;
   if (ptr_kind == ARNOLD_HOST) {
     int st = device_scratch(c);
@@ -421,6 +427,63 @@ int arnold_set_state(arnold_ctx* c, const double* x, const double* p, const doub
   c->launches++;
   c->steps = 0;
   if (ptr_kind == ARNOLD_HOST) ACHECK(cudaStreamSynchronize(c->stream));   // host buffers may be freed on return
+  return ARNOLD_OK;
+}
+
+int arnold_set_state(arnold_ctx* c, const double* x, const double* p, const double* w, int ptr_kind) {
+  return set_state_mode(c, x, p, w, ptr_kind, 0, 0.0);
+}
+
+int arnold_set_state_shell(arnold_ctx* c, const double* x, const double* p, int mode, double E, int ptr_kind) {
+  if (mode != ARNOLD_SHELL_DIRECTION && mode != ARNOLD_SHELL_PZ) return ARNOLD_EINVAL;
+  if (!isfinite(E)) return ARNOLD_EINVAL;
+  return set_state_mode(c, x, p, nullptr, ptr_kind, mode, E);
+}
+
+int arnold_track_patch(arnold_ctx* c, double cos_lo, double cos_hi, double phi_lo, double phi_hi) {
+  if (!c || !(cos_lo <= cos_hi) || !(phi_lo <= phi_hi) || !isfinite(cos_lo + cos_hi + phi_lo + phi_hi))
+    return ARNOLD_EINVAL;
+  ACHECK(cudaSetDevice(c->device));
+  if (!c->s.left) ACHECK(dalloc(&c->s.left, (size_t)c->n));
+  ACHECK(cudaMemsetAsync(c->s.left, 0, (size_t)c->n, c->stream));
+  c->s.patch[0] = cos_lo;
+  c->s.patch[1] = cos_hi;
+  c->s.patch[2] = phi_lo;
+  c->s.patch[3] = phi_hi;
+  return ARNOLD_OK;
+}
+
+int arnold_velocity_histogram(arnold_ctx* c, int n_cos, int n_phi, double cos_lo, double cos_hi, double phi_lo,
+                              double phi_hi, int filtered, uint64_t* counts, int ptr_kind, int accumulate) {
+  if (!c || !counts || n_cos <= 0 || n_phi <= 0 || (long long)n_cos * n_phi > (1LL << 28) || !(cos_lo < cos_hi) ||
+      !(phi_lo < phi_hi) || (ptr_kind != ARNOLD_HOST && ptr_kind != ARNOLD_DEVICE) || c->steps == 0)
+    return ARNOLD_EINVAL;
+  ACHECK(cudaSetDevice(c->device));
+  const size_t cells = (size_t)n_cos * n_phi;
+  int st = device_scratch(c);
+  if (st) return st;
+  st = read_indicator(c, ARNOLD_IND_V, c->scratch);
+  if (st) return st;
+  unsigned long long* d = (unsigned long long*)counts;
+  if (ptr_kind == ARNOLD_HOST) {
+    if (c->vhist_cells < cells) {
+      if (c->vhist) cudaFree(c->vhist);
+      c->vhist = nullptr;
+      c->vhist_cells = 0;
+      ACHECK(dalloc(&c->vhist, cells));
+      c->vhist_cells = cells;
+    }
+    d = c->vhist;
+    if (accumulate) ACHECK(cudaMemcpyAsync(d, counts, cells * 8, cudaMemcpyHostToDevice, c->stream));
+  }
+  if (!accumulate) ACHECK(cudaMemsetAsync(d, 0, cells * 8, c->stream));
+  const double p4[4] = {cos_lo, cos_hi, phi_lo, phi_hi};
+  ACHECK(launch_vhist(c->n, c->scratch, c->s.left, filtered, p4, n_cos, n_phi, d, grid_for(c, 256), c->stream));
+  c->launches++;
+  if (ptr_kind == ARNOLD_HOST) {
+    ACHECK(cudaMemcpyAsync(counts, d, cells * 8, cudaMemcpyDeviceToHost, c->stream));
+    return check_flags(c);
+  }
   return ARNOLD_OK;
 }
 

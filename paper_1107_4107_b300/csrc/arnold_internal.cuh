@@ -56,7 +56,19 @@ struct Fp64State {
   double* demax;   // [n]
   double* e0;      // [n] H at t = 0
   double* V;       // [3][n] V (x, y, z components) of the last closed window
+  unsigned char* left;  // [n] area tracking: 1 once the momentum direction left the patch (null = off)
+  double patch[4];      // cos_lo, cos_hi, phi_lo, phi_hi of the tracked patch
 };
+
+// Area tracking (Sec. IV, zooms of Fig. 3): is the momentum direction inside
+// [cos_lo, cos_hi] x [phi_lo, phi_hi] (phi = atan2(p_y, p_x) in [0, 2pi))?
+__device__ __forceinline__ bool inside_patch(double px, double py, double pz, const double* patch) {
+  const double m = sqrt(px * px + py * py + pz * pz);
+  const double c = pz / m;
+  double phi = atan2(py, px);
+  if (phi < 0.0) phi += kTwoPi;
+  return c >= patch[0] && c <= patch[1] && phi >= patch[2] && phi <= patch[3];
+}
 
 struct Fp32cState {
   float* hi;       // [6][n] u, v, z, q_u, q_v, p_z (leading parts)

@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(256) k_iterate_fp64(IterArgs a) {
         const double dE = fabs(energy64(t, a.eps, ssc, sth) - e0);
         demax = fmax(demax, dE);
         if (!isfinite(dE)) bad = 1;
+        if (a.s.left && !inside_patch(0.5 * (t.qu + t.qv), 0.5 * (t.qu - t.qv), t.pz, a.s.patch)) a.s.left[i] = 1;
       }
       if (a.W > 0 && --to_window == 0) {
         to_window = a.W;

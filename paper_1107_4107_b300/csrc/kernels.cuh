@@ -18,6 +18,7 @@ struct InitArgs {
   double E, eps, half_width;
   unsigned long long seed;
   int tangent;
+  int shell_mode;       // set_state: 0 P given, 1 P = |P| p (unit direction), 2 p_z from the energy
   int* flags;
 };
 
@@ -75,6 +76,8 @@ cudaError_t launch_sum2(long long n, const double* a, const double* b, double* p
                         cudaStream_t st);
 
 cudaError_t launch_set_state(const InitArgs& a, int grid, int block, cudaStream_t st);
+cudaError_t launch_vhist(long long n, const double* V, const unsigned char* left, int filtered, const double* patch4,
+                         int n_cos, int n_phi, unsigned long long* counts, int grid, cudaStream_t st);
 cudaError_t launch_init_grid(const InitArgs& a, int grid, int block, cudaStream_t st);
 cudaError_t launch_indicator(const ReadArgs& a, int grid, int block, cudaStream_t st);
 cudaError_t launch_debug_sincos64(const double* x, double* s, double* c, long long n, const double2* sc,

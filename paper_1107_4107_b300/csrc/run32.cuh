@@ -101,6 +101,10 @@ __device__ __forceinline__ void renorm_sample32(const RunArgs32& a, long long i,
   const double dE = fabs(H - a.s.e0[i]);
   demax = fmax(demax, dE);
   if (!isfinite(dE)) bad = 1;
+  if (a.s.left) {
+    const double qu = (double)t.qu.hi + (double)t.qu.lo, qv = (double)t.qv.hi + (double)t.qv.lo;
+    if (!inside_patch(0.5 * (qu + qv), 0.5 * (qu - qv), (double)t.pz.hi + (double)t.pz.lo, a.s.patch)) a.s.left[i] = 1;
+  }
 }
 
 // Close an averaging window of V (Sec. IV) for trajectory i.

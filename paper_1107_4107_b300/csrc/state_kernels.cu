@@ -58,6 +58,7 @@ __device__ __forceinline__ void init_common(const InitArgs& a, long long i, doub
   a.s.demax[i] = 0.0;
   if (a.s.logsum) a.s.logsum[i] = 0.0;
   a.s.V[i] = 0.0; a.s.V[n + i] = 0.0; a.s.V[2 * n + i] = 0.0;
+  if (a.s.left) a.s.left[i] = 0;
   if (a.tangent) {
     double w[6];
     if (a.w_in) {
@@ -92,7 +93,24 @@ __global__ void k_set_state(InitArgs a) {
     double u, v;
     int lu, lv;
     to_uv(x, y, u, v, lu, lv);
-    const double px = a.p_in[i], py = a.p_in[n + i], pz = a.p_in[2 * n + i];
+    double px = a.p_in[i], py = a.p_in[n + i], pz = a.p_in[2 * n + i];
+    if (a.shell_mode) {   // fixed-energy initial momenta (Sec. IV)
+      double su, cu, sv, cv, sz, cz;
+      sincos_tab64(u, a.sc, a.th, su, cu);
+      sincos_tab64(v, a.sc, a.th, sv, cv);
+      sincos_tab64(z, a.sc, a.th, sz, cz);
+      const double hp = (cu + cv) * (cz * cz);
+      if (a.shell_mode == 1) {          // P = sqrt(2 (E - eps Hp)) * unit direction
+        const double r = 2.0 * (a.E - a.eps * hp);
+        const double m = sqrt(r);
+        if (!(r >= 0.0)) atomicOr(a.flags, kFlagNonFinite);
+        px *= m; py *= m; pz *= m;
+      } else {                          // p_z = +sqrt(2 (E - eps Hp) - p_x^2 - p_y^2)
+        const double r = 2.0 * (a.E - a.eps * hp) - px * px - py * py;
+        pz = sqrt(r);
+        if (!(r >= 0.0)) atomicOr(a.flags, kFlagNonFinite);
+      }
+    }
     // the parity of lu + lv carries the pi offset of x and y; displacements
     // are measured from here, so earlier laps of x and y are not kept
     init_common(a, i, u, v, z, px + py, px - py, pz, lu, lv, lz);
@@ -200,6 +218,9 @@ __global__ void k_indicator(ReadArgs a) {
       case ARNOLD_IND_LOGSUM:
         out[i] = a.s.logsum[i];
         break;
+      case ARNOLD_IND_LEFT:
+        ((unsigned char*)a.out)[i] = a.s.left ? a.s.left[i] : 0;
+        break;
       case ARNOLD_IND_DE_MAX:
         out[i] = a.s.demax[i];
         break;
@@ -237,7 +258,35 @@ __global__ void k_debug_sincos(const double* x, double* s, double* c, long long 
   }
 }
 
+// Density of V on the momentum sphere (Sec. IV, F of Figs. 2-4): counts of the
+// direction of V in n_cos x n_phi equal-width cells of cos theta and phi over
+// the patch; directions outside the patch, and (filtered) trajectories that
+// left the tracked area, are not counted.
+__global__ void k_vhist(long long n, const double* V, const unsigned char* left, int filtered, double c0, double c1,
+                        double f0, double f1, int n_cos, int n_phi, unsigned long long* counts) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    if (filtered && left && left[i]) continue;
+    const double vx = V[i], vy = V[n + i], vz = V[2 * n + i];
+    const double m = sqrt(vx * vx + vy * vy + vz * vz);
+    const double c = vz / m;
+    double phi = atan2(vy, vx);
+    if (phi < 0.0) phi += kTwoPi;
+    if (!(c >= c0 && c <= c1 && phi >= f0 && phi <= f1)) continue;
+    int a = (int)((c - c0) / (c1 - c0) * n_cos);
+    int b = (int)((phi - f0) / (f1 - f0) * n_phi);
+    a = min(max(a, 0), n_cos - 1);
+    b = min(max(b, 0), n_phi - 1);
+    atomicAdd(&counts[(long long)a * n_phi + b], 1ULL);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_vhist(long long n, const double* V, const unsigned char* left, int filtered, const double* p4,
+                         int n_cos, int n_phi, unsigned long long* counts, int grid, cudaStream_t st) {
+  k_vhist<<<grid, 256, 0, st>>>(n, V, left, filtered, p4[0], p4[1], p4[2], p4[3], n_cos, n_phi, counts);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_set_state(const InitArgs& a, int grid, int block, cudaStream_t st) {
   k_set_state<<<grid, block, 0, st>>>(a);

@@ -96,3 +96,34 @@ def sample_cells(n_total: int, k: int, seed: int = 12345) -> np.ndarray:
     if len(picked) < k:
         raise ValueError("sample_cells: too few distinct draws")
     return np.sort(picked[:k])
+
+
+def sphere_directions(n: int, seed: int = 0, cos_range=(-1.0, 1.0), phi_range=(0.0, TWO_PI), offset: int = 0):
+    """Angles uniform on the torus and momentum directions uniform on a patch of
+    the unit sphere (cos theta uniform in cos_range, phi uniform in phi_range):
+    the ensembles of Sec. IV, Figs. 2-3 (whole sphere, or a segment for zooms).
+    Trajectory t draws counters 5t .. 5t+4.  Returns (X[3][n], nhat[3][n]);
+    the modulus of P is left to the fixed-energy step."""
+    t = np.arange(offset, offset + n, dtype=np.uint64)
+    c = np.uint64(5) * t
+    X = np.stack([angles(seed, c + np.uint64(k)) for k in range(3)])
+    u = uniform01(splitmix64(seed, c + np.uint64(3)))
+    w = uniform01(splitmix64(seed, c + np.uint64(4)))
+    ct = cos_range[0] + (cos_range[1] - cos_range[0]) * u
+    ph = phi_range[0] + (phi_range[1] - phi_range[0]) * w
+    st = np.sqrt(np.maximum(0.0, 1.0 - ct * ct))
+    return X, np.stack([st * np.cos(ph), st * np.sin(ph), ct])
+
+
+def gaussian_velocities(n: int, center=(0.0, 0.0), sigma: float = 0.01, seed: int = 0, offset: int = 0):
+    """Angles uniform on the torus, (p_x, p_y) Gaussian about `center` with
+    standard deviation sigma (Box-Muller on two SplitMix64 uniforms; the
+    ensemble of Fig. 4).  Counters 5t .. 5t+4.  Returns (X[3][n], Pxy[2][n]);
+    p_z is left to the fixed-energy step."""
+    t = np.arange(offset, offset + n, dtype=np.uint64)
+    c = np.uint64(5) * t
+    X = np.stack([angles(seed, c + np.uint64(k)) for k in range(3)])
+    u1 = 1.0 - uniform01(splitmix64(seed, c + np.uint64(3)))       # (0, 1]
+    u2 = uniform01(splitmix64(seed, c + np.uint64(4)))
+    r = np.sqrt(-2.0 * np.log(u1))
+    return X, np.stack([center[0] + sigma * r * np.cos(TWO_PI * u2), center[1] + sigma * r * np.sin(TWO_PI * u2)])

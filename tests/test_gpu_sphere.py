@@ -1,0 +1,85 @@
+"""Sphere ensembles, area tracking and the density of V on the momentum sphere
+(Sec. IV, Figs. 2-4) on the GPU against the oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1107_4107_b300 import inputs
+from parity import rel_err
+
+pytestmark = pytest.mark.gpu
+TWO_PI = 2 * math.pi
+
+
+def _ens(n, **kw):
+    from paper_1107_4107_b300.api import ArnoldEnsemble
+    return ArnoldEnsemble(n, **kw)
+
+
+def test_shell_initial_conditions():
+    n = 4096
+    X, nh = inputs.sphere_directions(n, seed=3)
+    e = _ens(n)
+    e.init_sphere(400.0, seed=3)
+    assert rel_err(e.indicator("P"), oracle.momenta_on_shell(400.0, 1.0, X, nh)) < 1e-14
+    X2, Pxy = inputs.gaussian_velocities(n, center=(math.sqrt(15.0) - 0.3, math.sqrt(15.0) - 0.3), sigma=0.01, seed=4)
+    e.init_gaussian(15.0, center=(math.sqrt(15.0) - 0.3, math.sqrt(15.0) - 0.3), sigma=0.01, seed=4)
+    P = np.zeros((3, n)); P[:2] = Pxy
+    assert rel_err(e.indicator("P"), oracle.pz_from_energy(15.0, 1.0, X2, P)) < 1e-14
+    assert np.max(e.indicator("dE")) < 1e-12 * 400
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_area_tracking_matches_oracle(precision):
+    """A patch of the sphere at E = 15 (moderate perturbation, Fig. 3): trajectories
+    flagged for leaving the patch at any sample every R = 10 steps."""
+    n, S, E = 3000, 300, 15.0
+    patch = (0.2, 0.45, 0.6, 1.1)
+    X, nh = inputs.sphere_directions(n, seed=8, cos_range=patch[:2], phi_range=patch[2:])
+    P = oracle.momenta_on_shell(E, 1.0, X, nh)
+    _, _, left = oracle.track_patch(oracle.Params(renorm_every=10), X, P, S, patch)
+    e = _ens(n, precision=precision, renorm_every=10)
+    e.init_sphere(E, seed=8, cos_range=patch[:2], phi_range=patch[2:])
+    e.track_patch(*patch)
+    e.iterate(S)
+    got = e.indicator("left")
+    assert 0.02 < left.mean() < 0.98
+    # FP64: identical up to decisions within rounding of the patch edge;
+    # FP32C: trajectories differ at ~1e-7, so a few edge crossings may differ
+    allowed = 3 if precision == "fp64" else max(10, n // 100)
+    assert int(np.sum(got != left)) <= allowed
+
+
+def test_velocity_histogram_matches_oracle():
+    n, S, E = 20000, 200, 400.0
+    X, nh = inputs.sphere_directions(n, seed=9)
+    st = oracle.State(X, oracle.momenta_on_shell(E, 1.0, X, nh), oracle.Params(), tangent=False)
+    st.advance(S, threads=8)
+    ref = oracle.velocity_histogram(st.velocity(), 24, 48)
+    e = _ens(n, tangent=False)
+    e.init_sphere(E, seed=9)
+    e.iterate(S)
+    got = e.velocity_histogram(24, 48)
+    assert got.sum() == ref.sum() == n
+    assert np.abs(got.astype(np.int64) - ref).sum() <= 4
+    # accumulation over two calls (time-averaged F) and the device path
+    got2 = e.velocity_histogram(24, 48, out=got.copy(), accumulate=True)
+    assert np.array_equal(got2, 2 * got)
+
+
+def test_filtered_histogram_counts_only_tracked_trajectories():
+    n, E = 5000, 15.0
+    patch = (0.2, 0.45, 0.6, 1.1)
+    e = _ens(n, tangent=False, renorm_every=5)
+    e.init_sphere(E, seed=10, cos_range=patch[:2], phi_range=patch[2:])
+    e.track_patch(*patch)
+    e.iterate(200)
+    left = e.indicator("left")
+    H = e.velocity_histogram(10, 10, patch=patch, filtered=True)
+    V = e.indicator("V")
+    c = V[2] / np.sqrt(np.sum(V * V, axis=0))
+    phi = np.mod(np.arctan2(V[1], V[0]), TWO_PI)
+    inside = (c >= patch[0]) & (c <= patch[1]) & (phi >= patch[2]) & (phi <= patch[3])
+    assert H.sum() == int(np.sum(inside & (left == 0)))
