@@ -1,0 +1,140 @@
+"""Experiment runners built on the hot path (paper Sec. III-IV).
+
+* throughput_vs_n: wall time of a fixed propagation time against the ensemble
+  size N (the measurement of Fig. 1; the paper's curve steps at multiples of
+  the number of realisations its GPU ran at once).
+* web_density: the Arnold-web picture of Figs. 2-3 - an ensemble uniform over
+  (a patch of) the momentum sphere, V over one window, F as a histogram of the
+  direction of V, optionally only trajectories that stayed in the patch.
+* diffusion_from_w: Fig. 4 - a Gaussian cloud at the triple resonance
+  W = (sqrt E, sqrt E, 0), windows of dt, F time-averaged between snapshots,
+  with checkpoint/resume for long horizons.
+"""
+from __future__ import annotations
+
+import math
+import os
+
+import numpy as np
+
+from . import _lib
+from .api import ArnoldEnsemble
+from .params import paper_h
+
+T = 2.0 * math.pi
+
+
+def throughput_vs_n(ns, steps: int = 200, precision: str = "fp64", E: float = 400.0, tangent: bool = True,
+                    device: int = 0) -> list[dict]:
+    """Time `steps` composite steps for each ensemble size in ns (sphere ICs at E)."""
+    import torch
+    out = []
+    for n in ns:
+        e = ArnoldEnsemble(int(n), precision=precision, tangent=tangent, device=device)
+        e.init_sphere(E, seed=1)
+        e.iterate(min(steps, 10))
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        e.iterate(steps)
+        b.record()
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        out.append({"n": int(n), "ms": ms, "ms_per_step": ms / steps, "map_steps_per_s": n * steps / (ms * 1e-3)})
+        e.close()
+    return out
+
+
+def web_density(n: int, E: float, window_T: float = 50.0, n_cos: int = 256, n_phi: int = 512,
+                patch=(-1.0, 1.0, 0.0, 2 * math.pi), track: bool = False, precision: str = "fp32c",
+                seed: int = 0, h: float | None = None, device: int = 0) -> dict:
+    """Figs. 2-3: ICs uniform over the patch of S and over the torus, propagated
+    for t_p = dt = window_T periods; returns the counts of V's direction on the
+    patch (and the fraction of trajectories kept by the area filter)."""
+    h = paper_h() if h is None else h
+    steps = int(round(window_T * T / h))
+    e = ArnoldEnsemble(n, precision=precision, tangent=False, h=h, window=steps, device=device)
+    e.init_sphere(E, seed=seed, cos_range=patch[:2], phi_range=patch[2:])
+    if track:
+        e.track_patch(*patch)
+    e.iterate(steps)
+    counts = e.velocity_histogram(n_cos, n_phi, patch=patch, filtered=track)
+    kept = 1.0 - float(np.mean(e.indicator("left"))) if track else 1.0
+    e.sync()
+    return {"counts": counts, "steps": steps, "kept_fraction": kept, "n": n, "E": E}
+
+
+def diffusion_from_w(n: int = 32000, E: float = 15.0, sigma: float = 0.01, window_T: float = 50.0,
+                     snapshots_T=(1e2, 1e3, 1e4), n_cos: int = 128, n_phi: int = 256, precision: str = "fp32c",
+                     seed: int = 0, ckpt_path: str | None = None, device: int = 0, h: float | None = None) -> dict:
+    """Fig. 4: the cloud starts at W = (sqrt E, sqrt E, 0) with Gaussian (p_x, p_y)
+    of width sigma and p_z from the energy; angles whose energy condition has no
+    real p_z are redrawn (the cloud sits where |P|^2 = 2E, so the potential must
+    be <= 0 there).  F of V over windows of window_T is accumulated between
+    consecutive snapshot times (time-averaged F).  With ckpt_path the state is
+    saved after every window and a rerun resumes from it."""
+    h = paper_h() if h is None else h
+    W = math.sqrt(E)
+    w_steps = int(round(window_T * T / h))
+    e = init_gaussian_valid(n, E, (W, W), sigma, seed, precision=precision, window=w_steps, h=h, device=device)
+    done_windows = 0
+    maps = []
+    acc = np.zeros((n_cos, n_phi), dtype=np.uint64)
+    if ckpt_path and os.path.exists(ckpt_path):
+        blob = open(ckpt_path, "rb").read()
+        e.restore(blob[:-16])
+        done_windows = int(np.frombuffer(blob[-16:-8], dtype=np.int64)[0])
+        acc_path = ckpt_path + ".acc.npy"
+        if os.path.exists(acc_path):
+            acc = np.load(acc_path)
+    bounds = [int(round(s * T / h / w_steps)) for s in snapshots_T]
+    k = 0
+    while k < len(bounds) and bounds[k] <= done_windows:
+        k += 1
+    while k < len(bounds):
+        e.iterate(w_steps)
+        done_windows += 1
+        e.velocity_histogram(n_cos, n_phi, out=acc, accumulate=True)
+        if done_windows == bounds[k]:
+            maps.append({"t_T": snapshots_T[k], "counts": acc.copy()})
+            acc[:] = 0
+            k += 1
+        if ckpt_path:
+            with open(ckpt_path, "wb") as f:
+                f.write(e.checkpoint() + np.array([done_windows, 0], dtype=np.int64).tobytes())
+            np.save(ckpt_path + ".acc.npy", acc)
+    e.sync()
+    return {"maps": maps, "windows": done_windows, "n": n, "E": E, "window_steps": w_steps}
+
+
+def init_gaussian_valid(n: int, E: float, center, sigma: float, seed: int, **kw) -> ArnoldEnsemble:
+    """Gaussian cloud with p_z from the energy, redrawing the draws whose energy
+    condition has no real solution: candidates are placed on the device, those
+    with finite p_z kept in order until n are found."""
+    from .inputs import gaussian_velocities
+    Xs, Ps = [], []
+    have, offset, batch = 0, 0, max(2 * n, 1024)
+    probe = ArnoldEnsemble(batch, tangent=False, device=kw.get("device", 0))
+    while have < n:
+        X, Pxy = gaussian_velocities(batch, center, sigma, seed, offset=offset)
+        P = np.zeros((3, batch))
+        P[:2] = Pxy
+        probe.set_state_shell(X, P, _lib.SHELL_PZ, E)
+        # read through a device buffer: the host read would report the
+        # (expected) non-finite candidates as an error
+        import torch
+        Pd = torch.empty((3, batch), device=f"cuda:{kw.get('device', 0)}", dtype=torch.float64)
+        probe.indicator("P", out=Pd)
+        Pfull = Pd.cpu().numpy()
+        ok = np.isfinite(Pfull[2])
+        Xs.append(X[:, ok])
+        Ps.append(Pfull[:, ok])
+        have += int(ok.sum())
+        offset += batch
+    probe.close()
+    X = np.ascontiguousarray(np.concatenate(Xs, axis=1)[:, :n])
+    P = np.ascontiguousarray(np.concatenate(Ps, axis=1)[:, :n])
+    e = ArnoldEnsemble(n, tangent=False, **kw)
+    e.set_state(X, P)
+    return e
