@@ -43,10 +43,14 @@ HORIZON = 1_000_000
 # drift = 6 FMA (6 / 12); 7 kicks + 8 drifts.
 FP64_INSTR_PER_STEP = 7 * (3 * 10 + 8 + 14) + 8 * 6
 FP64_FLOP_PER_STEP = 7 * (3 * 16 + 11 + 22) + 8 * 12
-# FP32C: FP32-pipe instructions per composite step (iterate_fp32c.cu): kick =
-# 3 sincos (10 each) + force with TwoSum adds (5 + 3 + 3 * 7) + tangent (14);
-# drift = 3 * (4 product + 6 TwoSum + 2) + 3 tangent; 6 Fast2Sum renormalisations.
-FP32C_INSTR_PER_STEP = 7 * (3 * 10 + 29 + 14) + 8 * (3 * 12 + 3) + 6 * 3
+# FP32C: FP32/INT arithmetic per composite step counted from the source
+# (step32.cuh): kick = 3 sincos (12 each) + force with TwoSum adds (5 + 3 +
+# 3 * 7) + tangent (14); drift = 3 * (4 product + 6 TwoSum + 2) + 3 tangent;
+# end of step = 6 Fast2Sum renormalisations + the reduction test.
+FP32C_INSTR_PER_STEP = 7 * (3 * 12 + 29 + 14) + 8 * (3 * 12 + 3) + 6 * 3 + 6
+# Measured by ncu for k_iterate_fp32c<7,true,false> (all pipes, per map step):
+# profiles/k_iterate_fp32c__grid2048_E400_1M_traj_400_steps.md
+FP32C_ISSUED_PER_STEP_NCU = 1024
 
 
 def parse():
@@ -312,7 +316,10 @@ def main():
                  "roofline": {"bound": "alu", "kernel": "k_iterate_fp32c<7,true,false>",
                               "achieved_instr_per_s": v3 * FP32C_INSTR_PER_STEP, "peak_instr_per_s": ffma,
                               "frac": v3 * FP32C_INSTR_PER_STEP / ffma,
-                              "peak_source": "measured live: FFMA probe", "instr_per_map_step": FP32C_INSTR_PER_STEP},
+                              "issue_frac": v3 * FP32C_ISSUED_PER_STEP_NCU / ffma,
+                              "peak_source": "measured live: FFMA probe (1 warp instruction / clock / SMSP = the "
+                                             "issue peak)", "instr_per_map_step": FP32C_INSTR_PER_STEP,
+                              "issued_instr_per_map_step_ncu": FP32C_ISSUED_PER_STEP_NCU},
                  "agreement_note": "class agreement and histogram L1 vs FP64 are checked in tests/test_gpu_fp32c.py"}
         e3.close()
 
@@ -346,24 +353,36 @@ def adjoint_leg(stream, device, barrier):
     X, P = inputs.box(n, seed=0)
     Xd = torch.tensor(X, device="cuda")
     Pd = torch.tensor(P, device="cuda")
-    out = {"config": "65,536 box trajectories (E ~ 390), N = 1e4, 100 checkpoints, variance loss"}
+    out = {"config": "65,536 box trajectories (E ~ 390), N = 1e4, 100 checkpoints, variance loss; "
+                     "forward and reverse timed separately after a warm-up run (the upstream dL/dP_N is formed "
+                     "with torch between them)"}
+
+    def upstream(ens, m):
+        PN = torch.empty((3, m), device="cuda", dtype=torch.float64)
+        ens.indicator("P", out=PN)
+        return ((2.0 / 3.0) * (PN - PN.mean(dim=1, keepdim=True)) / m).contiguous()
+
     for prec in ("fp64", "fp32c"):
+        w = ArnoldEnsemble(1024, precision=prec, tangent=False, device=device, stream=stream.cuda_stream)
+        w.set_state(Xd[:, :1024].contiguous(), Pd[:, :1024].contiguous())
+        w.forward_ckpt(200, 10)
+        w.grad(dL_dp=upstream(w, 1024))
+        w.close()
         ens = ArnoldEnsemble(n, precision=prec, tangent=False, device=device, stream=stream.cuda_stream)
         ens.set_state(Xd, Pd)
         barrier()
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0, e1, e2, e3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
         e0.record(stream)
         ens.forward_ckpt(N, 100)
         e1.record(stream)
-        PN = torch.empty((3, n), device="cuda", dtype=torch.float64)
-        ens.indicator("P", out=PN)
-        up = (2.0 / 3.0) * (PN - PN.mean(dim=1, keepdim=True)) / n
-        gx, gp, gh, ge = ens.grad(dL_dp=up.contiguous())
+        up = upstream(ens, n)
         e2.record(stream)
+        gx, gp, gh, ge = ens.grad(dL_dp=up)
+        e3.record(stream)
         barrier()
-        fwd, tot = e0.elapsed_time(e1), e0.elapsed_time(e2)
-        out[prec] = {"value": n * N / (tot * 1e-3), "unit": "map-steps/s (forward + adjoint)",
-                     "forward_ms": fwd, "reverse_ms": tot - fwd, "dL_dh": float(gh), "dL_deps": float(ge)}
+        fwd, rev = e0.elapsed_time(e1), e2.elapsed_time(e3)
+        out[prec] = {"value": n * N / ((fwd + rev) * 1e-3), "unit": "map-steps/s (forward + adjoint)",
+                     "forward_ms": fwd, "reverse_ms": rev, "dL_dh": float(gh), "dL_deps": float(ge)}
         ens.close()
     return out
 
