@@ -138,3 +138,28 @@ def init_gaussian_valid(n: int, E: float, center, sigma: float, seed: int, **kw)
     e = ArnoldEnsemble(n, tangent=False, **kw)
     e.set_state(X, P)
     return e
+
+
+SWEEP_NS = [1, 32, 148, 1024, 4736, 9472, 9473, 18944, 37888, 75776, 151552, 151553, 303104, 606208, 1048576,
+            4194304, 10000000]
+
+
+def main(argv=None):
+    """python -m paper_1107_4107_b300.experiments sweep   -> JSON lines of throughput_vs_n."""
+    import json
+    import sys
+    args = sys.argv[1:] if argv is None else argv
+    if not args or args[0] != "sweep":
+        raise SystemExit("usage: python -m paper_1107_4107_b300.experiments sweep")
+    for prec in ("fp64", "fp32c"):
+        small = [n for n in SWEEP_NS if n <= 606208]
+        big = [n for n in SWEEP_NS if n > 606208]
+        rows = throughput_vs_n(small, steps=200 if prec == "fp64" else 1000, precision=prec)
+        rows += throughput_vs_n(big, steps=50 if prec == "fp64" else 400, precision=prec)
+        for r in rows:
+            r["precision"] = prec
+            print(json.dumps(r), flush=True)
+
+
+if __name__ == "__main__":
+    main()
