@@ -48,6 +48,7 @@ extern "C" {
 #define ARNOLD_ENONFINITE   -5  /* the state became NaN/Inf (checked when results are read)         */
 #define ARNOLD_EUNSUPPORTED -6  /* combination not built (e.g. no CUDA device)                      */
 #define ARNOLD_ESTATE       -7  /* call out of order (e.g. arnold_grad before arnold_forward_ckpt)  */
+#define ARNOLD_ERANGE       -8  /* outside the precision mode's range (DF64: h |q| > 9 per step)    */
 
 /* ---- enums --------------------------------------------------------------- */
 /* Integrators (Sec. III names a sixth-order symplectic scheme whose reference
@@ -58,6 +59,8 @@ extern "C" {
 
 #define ARNOLD_FP64  0  /* state, tangent and sincos in FP64 (the paper used double precision, Sec. III) */
 #define ARNOLD_FP32C 1  /* compensated FP32: two-sum angle/action updates, FP64 angle reduction and logs   */
+#define ARNOLD_DF64  2  /* double-float: state and kicks in float pairs (~48-bit), FP64-grade trajectories
+                           on the FP32 pipes; tangent in FP32.  No adjoint or batch.                   */
 
 #define ARNOLD_HOST   0
 #define ARNOLD_DEVICE 1
@@ -80,7 +83,7 @@ typedef struct arnold_params {
   double  eps;           /* eps of Eq. 1 (the paper uses 1, Eq. 3)                          */
   double  h;             /* composite step, != 0 (paper: 0.01 * 2 pi, Sec. III)             */
   int32_t scheme;        /* ARNOLD_SCHEME_*                                                 */
-  int32_t precision;     /* ARNOLD_FP64 or ARNOLD_FP32C                                     */
+  int32_t precision;     /* ARNOLD_FP64, ARNOLD_FP32C or ARNOLD_DF64                        */
   int32_t tangent;       /* 1: carry the tangent vector and FTLE; 0: state only            */
   int32_t renorm_every;  /* R >= 1: tangent renormalisation / energy sampling interval      */
   int64_t window;        /* W >= 0: steps per averaging window of V; 0 = whole run          */

@@ -11,9 +11,9 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libarnold.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, EUNSUPPORTED, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, EUNSUPPORTED, ESTATE, ERANGE = 0, -1, -2, -3, -4, -5, -6, -7, -8
 SCHEMES = {"yoshida6a": 0, "triplejump6": 1, "leapfrog2": 2}
-PRECISIONS = {"fp64": 0, "fp32c": 1}
+PRECISIONS = {"fp64": 0, "fp32c": 1, "df64": 2}
 HOST, DEVICE = 0, 1
 IND = {"chi": 0, "V": 1, "dE": 2, "dE_max": 3, "class": 4, "X": 5, "P": 6, "dX": 7, "tangent": 8, "logsum": 9,
        "left": 10}

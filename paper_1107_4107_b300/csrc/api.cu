@@ -9,6 +9,7 @@
 
 #include "kernels.cuh"
 #include "run32.cuh"
+#include "step_df.cuh"
 
 namespace arnold {
 cudaError_t launch_iterate_fp32c_v(const IterArgs& a, int scheme, bool tangent, bool reduce64, int block, int grid,
@@ -23,6 +24,27 @@ static long double round_bits(long double x, int bits) {
 
 // FP32 table geometry (see Tab32 in step32.cuh): D = 2 pi / 2048 split into
 // d1 (7 significant bits) + d2 + d3, 2 pi split into c1 + c2 (18 bits each) + c3.
+// DF64 table geometry (TabDF in step_df.cuh): D = 2 pi / 2048 split d1 (11
+// significant bits) + d2 + d3; 2 pi split as for the FP32 table.
+void df_tab(TabDF* tb) {
+  const long double two_pi = 6.283185307179586476925286766559005768L;
+  const long double D = two_pi / 2048.0L;
+  const long double d1 = round_bits(D, 11);
+  const float d2 = (float)(D - d1);
+  const float d3 = (float)(D - d1 - (long double)d2);
+  tb->inv_d = (float)(1.0L / D);
+  tb->d1 = (float)d1;
+  tb->d2 = d2;
+  tb->d3 = d3;
+  tb->mask = 2047;
+  tb->inv2pi = (float)(1.0L / two_pi);
+  const long double c1 = round_bits(two_pi, 18);
+  const long double c2 = round_bits(two_pi - c1, 18);
+  tb->c1 = (float)c1;
+  tb->c2 = (float)c2;
+  tb->c3 = (float)(two_pi - c1 - c2);
+}
+
 void fp32_tab(Tab32* tb) {
   const long double two_pi = 6.283185307179586476925286766559005768L;
   const long double D = two_pi / 2048.0L;
@@ -58,6 +80,7 @@ struct arnold_ctx {
   double2* sc = nullptr;   // FP64 sincos table
   double* th = nullptr;
   float2* scf = nullptr;   // FP32 sincos table
+  float4* scd = nullptr;   // DF64 sincos table
   int* flags = nullptr;    // device error flags
   StatsPartial* partials = nullptr;
   StatsPartial* stats_out = nullptr;
@@ -104,7 +127,7 @@ int params_ok(const arnold_params* p) {
   if (!p) return 0;
   if (!(p->h != 0.0) || !isfinite(p->h) || !isfinite(p->eps)) return 0;
   if (p->scheme < 0 || p->scheme > 2) return 0;
-  if (p->precision != ARNOLD_FP64 && p->precision != ARNOLD_FP32C) return 0;
+  if (p->precision != ARNOLD_FP64 && p->precision != ARNOLD_FP32C && p->precision != ARNOLD_DF64) return 0;
   if (p->tangent != 0 && p->tangent != 1) return 0;
   if (p->renorm_every < 1 || p->window < 0) return 0;
   if (!(p->chaos_kappa > 0.0)) return 0;
@@ -196,6 +219,21 @@ int build_tables(arnold_ctx* c) {
   e = cudaMalloc(&c->scf, sizeof(float2) * (jmax + 1));
   if (e == cudaSuccess) e = cudaMemcpy(c->scf, hf, sizeof(float2) * (jmax + 1), cudaMemcpyHostToDevice);
   free(hf);
+  if (e != cudaSuccess) return cuda_status(e);
+  // DF64 table: (sin, cos)(2 pi j / 2048) as float pairs
+  float4* hd = (float4*)malloc(sizeof(float4) * 2048);
+  if (!hd) return ARNOLD_ENOMEM;
+  for (int j = 0; j < 2048; ++j) {
+    const long double t = (long double)j * (6.283185307179586476925286766559005768L / 2048.0L);
+    const long double sv = sinl(t), cv = cosl(t);
+    hd[j].x = (float)sv;
+    hd[j].y = (float)(sv - (long double)hd[j].x);
+    hd[j].z = (float)cv;
+    hd[j].w = (float)(cv - (long double)hd[j].z);
+  }
+  e = cudaMalloc(&c->scd, sizeof(float4) * 2048);
+  if (e == cudaSuccess) e = cudaMemcpy(c->scd, hd, sizeof(float4) * 2048, cudaMemcpyHostToDevice);
+  free(hd);
   return cuda_status(e);
 }
 
@@ -206,7 +244,7 @@ cudaError_t dalloc(T** p, size_t count) {
 
 void free_all(arnold_ctx* c) {
   void* ptrs[] = {c->s.st, c->s.tg, c->s.lap, c->s.lapref, c->s.ref, c->s.logsum, c->s.demax, c->s.e0, c->s.V,
-                  c->f.hi, c->f.lo, c->f.tg, c->sc, c->th, c->scf, c->flags, c->partials, c->stats_out,
+                  c->f.hi, c->f.lo, c->f.tg, c->sc, c->th, c->scf, c->scd, c->flags, c->partials, c->stats_out,
                   c->scratch, c->scratch2, c->ck, c->seg, c->lam, c->lamf, c->gh, c->ge, c->sum_part, c->s.left,
                   c->vhist};
   for (void* p : ptrs)
@@ -225,6 +263,7 @@ int check_flags(arnold_ctx* c) {
   ACHECK(cudaMemcpyAsync(&h, c->flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   ACHECK(cudaStreamSynchronize(c->stream));
   if (h & kFlagTimeout) return ARNOLD_ETIMEOUT;
+  if (h & kFlagRange) return ARNOLD_ERANGE;
   if (h & kFlagNonFinite) return ARNOLD_ENONFINITE;
   return ARNOLD_OK;
 }
@@ -258,7 +297,7 @@ int read_indicator(arnold_ctx* c, int kind, void* dst) {
   r.n = c->n;
   r.W = c->prm.window;
   r.kind = kind;
-  r.fp32c = c->prm.precision == ARNOLD_FP32C;
+  r.fp32c = c->prm.precision != ARNOLD_FP64;   // pair state
   r.t = (double)c->steps * c->prm.h;
   r.eps = c->prm.eps;
   const double tt = fabs(r.t);
@@ -329,6 +368,7 @@ const char* arnold_strerror(int s) {
     case ARNOLD_ENONFINITE: return "non-finite state";
     case ARNOLD_EUNSUPPORTED: return "unsupported (no CUDA device or combination not built)";
     case ARNOLD_ESTATE: return "call out of order";
+    case ARNOLD_ERANGE: return "parameters outside the range of the precision mode";
   }
   return "unknown status";
 }
@@ -351,7 +391,7 @@ int arnold_create(const arnold_params* prm, int64_t n_traj, int device, void* cu
   const size_t n = (size_t)n_traj;
   const int tan = prm->tangent;
   cudaError_t e = cudaSuccess;
-  if (prm->precision == ARNOLD_FP64) {
+  if (prm->precision == ARNOLD_FP64) {   // FP32C and DF64 keep float pairs
     e = dalloc(&c->s.st, 6 * n);
     if (e == cudaSuccess && tan) e = dalloc(&c->s.tg, 6 * n);
   } else {
@@ -516,6 +556,7 @@ int arnold_iterate(arnold_ctx* c, int64_t n_steps) {
   ACHECK(cudaSetDevice(c->device));
   const arnold_params& p = c->prm;
   const bool fp32c = p.precision == ARNOLD_FP32C;
+  const bool df64 = p.precision == ARNOLD_DF64;
   int block = p.block_size;
   if (block == 0) {
     block = 256;
@@ -523,14 +564,16 @@ int arnold_iterate(arnold_ctx* c, int64_t n_steps) {
     if (per_sm < 256) block = (int)((per_sm + 31) / 32 * 32);
     if (block < 32) block = 32;
   }
-  const int bps = fp32c ? fp32c_blocks_per_sm(p.scheme, p.tangent, block) : fp64_blocks_per_sm(p.scheme, p.tangent, block);
+  const int bps = fp32c  ? fp32c_blocks_per_sm(p.scheme, p.tangent, block)
+                  : df64 ? df64_blocks_per_sm(p.scheme, p.tangent, block)
+                         : fp64_blocks_per_sm(p.scheme, p.tangent, block);
   long long grid = (c->n + block - 1) / block;
   const long long cap = (long long)c->sms * bps;
   if (grid > cap) grid = cap;
   long long chunk = p.launch_steps;
   if (chunk == 0) {
     // aim at ~0.2 s per launch from the measured rates (map-steps/s, 7 kicks)
-    const double rate = (fp32c ? 3.0e10 : 1.0e9) * 7.0 / (double)make_coef(p).m;
+    const double rate = (fp32c ? 3.0e10 : (df64 ? 8.0e9 : 1.0e9)) * 7.0 / (double)make_coef(p).m;
     chunk = (long long)(0.2 * rate / (double)c->n);
     if (chunk < 1) chunk = 1;
     if (chunk > (1 << 20)) chunk = 1 << 20;
@@ -542,6 +585,7 @@ int arnold_iterate(arnold_ctx* c, int64_t n_steps) {
   a.sc = c->sc;
   a.th = c->th;
   a.scf = c->scf;
+  a.scd = c->scd;
   a.n = c->n;
   a.R = p.renorm_every;
   a.W = p.window;
@@ -554,8 +598,9 @@ int arnold_iterate(arnold_ctx* c, int64_t n_steps) {
     const long long s = left < chunk ? left : chunk;
     a.step0 = c->steps;
     a.nsteps = (int)s;
-    cudaError_t e = fp32c ? launch_iterate_fp32c_v(a, p.scheme, p.tangent, c->reduce64, block, (int)grid, c->stream)
-                          : launch_iterate_fp64(a, p.scheme, p.tangent, block, (int)grid, c->stream);
+    cudaError_t e = fp32c  ? launch_iterate_fp32c_v(a, p.scheme, p.tangent, c->reduce64, block, (int)grid, c->stream)
+                    : df64 ? launch_iterate_df64(a, p.scheme, p.tangent, block, (int)grid, c->stream)
+                           : launch_iterate_fp64(a, p.scheme, p.tangent, block, (int)grid, c->stream);
     if (e != cudaSuccess) return cuda_status(e);
     c->launches++;
     c->steps += s;
@@ -643,7 +688,7 @@ static int ensure_bytes(void** p, size_t* have, size_t need) {
 
 int arnold_forward_ckpt(arnold_ctx* c, int64_t n_steps, int64_t ckpt_every) {
   if (!c || n_steps < 1 || ckpt_every < 0) return ARNOLD_EINVAL;
-  if (c->prm.precision == ARNOLD_FP32C && c->reduce64) return ARNOLD_EUNSUPPORTED;
+  if ((c->prm.precision == ARNOLD_FP32C && c->reduce64) || c->prm.precision == ARNOLD_DF64) return ARNOLD_EUNSUPPORTED;
   ACHECK(cudaSetDevice(c->device));
   long long C = ckpt_every > 0 ? ckpt_every : (long long)ceil(sqrt((double)n_steps));
   if (C > n_steps) C = n_steps;
@@ -872,7 +917,8 @@ int arnold_sync(arnold_ctx* c) {
 int arnold_debug_sincos(arnold_ctx* c, int precision, int64_t n, const double* x, double* s, double* co) {
   if (!c || !x || !s || !co || n <= 0) return ARNOLD_EINVAL;
   ACHECK(cudaSetDevice(c->device));
-  cudaError_t e = precision == ARNOLD_FP32C ? launch_debug_sincos32(x, s, co, n, c->scf, c->stream)
+  cudaError_t e = precision == ARNOLD_FP32C  ? launch_debug_sincos32(x, s, co, n, c->scf, c->stream)
+                 : precision == ARNOLD_DF64 ? launch_debug_sincos_df(x, s, co, n, c->scd, c->stream)
                                             : launch_debug_sincos64(x, s, co, n, c->sc, c->th, c->stream);
   ACHECK(e);
   c->launches++;

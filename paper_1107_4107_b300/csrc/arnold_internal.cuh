@@ -44,7 +44,7 @@ struct StepCoef {
 };
 
 // Device-side error flags (bits of one int, set with atomicOr, read by the host).
-enum : int { kFlagNonFinite = 1, kFlagTimeout = 2, kFlagBadIndex = 4 };
+enum : int { kFlagNonFinite = 1, kFlagTimeout = 2, kFlagBadIndex = 4, kFlagRange = 8 };
 
 struct Fp64State {
   double* st;      // [6][n] u, v, z, q_u, q_v, p_z (null for FP32C contexts)
@@ -82,6 +82,7 @@ struct IterArgs {
   const double2* sc;   // FP64 sincos table
   const double* th;
   const float2* scf;   // FP32 sincos table
+  const float4* scd;   // DF64 sincos table (sin hi, sin lo, cos hi, cos lo)
   long long n;
   long long step0;     // steps taken before this launch
   int nsteps;          // steps in this launch
@@ -97,7 +98,9 @@ cudaError_t launch_iterate_fp64(const IterArgs& a, int scheme, bool tangent, int
                                 cudaStream_t st);
 cudaError_t launch_iterate_fp32c(const IterArgs& a, int scheme, bool tangent, int block, int grid,
                                  cudaStream_t st);
+cudaError_t launch_iterate_df64(const IterArgs& a, int scheme, bool tangent, int block, int grid, cudaStream_t st);
 int fp64_blocks_per_sm(int scheme, bool tangent, int block);
+int df64_blocks_per_sm(int scheme, bool tangent, int block);
 int fp32c_blocks_per_sm(int scheme, bool tangent, int block);
 
 }  // namespace arnold

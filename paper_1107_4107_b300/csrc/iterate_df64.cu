@@ -1,0 +1,167 @@
+// DF64 ensemble propagator: FP64-grade trajectories on the FP32 pipes.
+//
+// Same composite step and state layout as the compensated-FP32 path (float
+// pairs for angles and momenta, exact TwoProd/TwoSum drifts), but every kick
+// is evaluated in double-float (step_df.cuh): table sincos with the reduced
+// argument kept as a pair and the force products split exactly, so the map
+// is followed to ~1e-16 per operation like the FP64 kernel.  The tangent
+// vector stays in FP32 (its renormalisation logs in FP64).
+#include "kernels.cuh"
+#include "run32.cuh"
+#include "step_df.cuh"
+
+namespace arnold {
+
+namespace {
+
+struct CoefDF {
+  float sh[10], sl[10];   // drifts as float pairs
+  Pair k2[9];             // 2 tau eps as pairs
+  float k4f[9];
+};
+
+template <int M, bool TAN>
+__global__ void __launch_bounds__(256) k_iterate_df64(IterArgs a, TabDF tb, CoefDF cf) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float4* stab = reinterpret_cast<float4*>(smem);
+  for (int k = threadIdx.x; k <= tb.mask; k += blockDim.x) stab[k] = a.scd[k];
+  __syncthreads();
+  RunArgs32 ra;
+  ra.s = a.s;
+  ra.f = a.f;
+  ra.n = a.n;
+  ra.R = a.R;
+  ra.W = a.W;
+  ra.h = a.h;
+  ra.eps = a.eps;
+  ra.flags = a.flags;
+  const float hf = (float)a.h;
+  const long long n = a.n;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    Traj32 t;
+    double logsum, demax;
+    load32<TAN>(ra, i, t, logsum, demax);
+    int to_renorm = a.R - (int)(a.step0 % a.R);
+    long long to_window = a.W > 0 ? a.W - a.step0 % a.W : 0;
+    int bad = 0;
+#pragma unroll 1
+    for (int s = 0; s < a.nsteps; ++s) {
+      drift32<TAN>(t, cf.sh[0], cf.sl[0]);
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        kick_df<TAN>(t, cf.k2[k], cf.k4f[k], stab, tb);
+        drift32<TAN>(t, cf.sh[k + 1], cf.sl[k + 1]);
+      }
+      end_step_df(t, tb);
+      if (--to_renorm == 0) {
+        to_renorm = a.R;
+        if (TAN) {
+          const float n2 = 0.5f * (t.du * t.du + t.dv * t.dv) + t.dz * t.dz +
+                           0.5f * (t.dqu * t.dqu + t.dqv * t.dqv) + t.dpz * t.dpz;
+          logsum += 0.5 * (double)__logf(n2);
+          const float inv = rsqrtf(n2);
+          t.du *= inv; t.dv *= inv; t.dz *= inv;
+          t.dqu *= inv; t.dqv *= inv; t.dpz *= inv;
+          if (!(n2 > 0.0f) || !isfinite(n2)) bad = 1;
+        }
+        const double kin = 0.25 * (pair_sq_d(t.qu) + pair_sq_d(t.qv)) + 0.5 * pair_sq_d(t.pz);
+        const double dE = fabs(kin + a.eps * potential_df(t, stab, tb) - a.s.e0[i]);
+        demax = fmax(demax, dE);
+        if (!isfinite(dE)) bad = 1;
+        // the table's exact index range needs |angle| < 12.5 inside a step
+        const float qmax = fmaxf(fmaxf(fabsf(t.qu.hi), fabsf(t.qv.hi)), fabsf(t.pz.hi));
+        if (qmax * fabsf(hf) > 9.0f) atomicOr(a.flags, kFlagRange);
+        if (a.s.left) {
+          const double qu = (double)t.qu.hi + (double)t.qu.lo, qv = (double)t.qv.hi + (double)t.qv.lo;
+          if (!inside_patch(0.5 * (qu + qv), 0.5 * (qu - qv), (double)t.pz.hi + (double)t.pz.lo, a.s.patch))
+            a.s.left[i] = 1;
+        }
+      }
+      if (a.W > 0 && --to_window == 0) {
+        to_window = a.W;
+        close_window32(ra, i, t);
+      }
+    }
+    store32<TAN>(ra, i, t, logsum, demax);
+    if (bad) atomicOr(a.flags, kFlagNonFinite);
+  }
+}
+
+template <int M, bool TAN>
+cudaError_t launch_one(const IterArgs& a, const TabDF& tb, const CoefDF& cf, int block, int grid, cudaStream_t st) {
+  const size_t smem = (size_t)(tb.mask + 1) * sizeof(float4);
+  k_iterate_df64<M, TAN><<<grid, block, smem, st>>>(a, tb, cf);
+  return cudaGetLastError();
+}
+
+template <int M, bool TAN>
+int occ_one(const TabDF& tb, int block) {
+  int nb = 0;
+  const size_t smem = (size_t)(tb.mask + 1) * sizeof(float4);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_iterate_df64<M, TAN>, block, smem) != cudaSuccess) return 1;
+  return nb > 0 ? nb : 1;
+}
+
+CoefDF coef_df(const StepCoef& c) {
+  CoefDF r;
+  for (int k = 0; k < 10; ++k) { r.sh[k] = c.sig_hi[k]; r.sl[k] = c.sig_lo[k]; }
+  for (int k = 0; k < 9; ++k) {
+    r.k2[k].hi = (float)c.k2[k];
+    r.k2[k].lo = (float)(c.k2[k] - (double)r.k2[k].hi);
+    r.k4f[k] = c.k4f[k];
+  }
+  return r;
+}
+
+__global__ void k_debug_sincos_df(const double* x, double* s, double* c, long long n, const float4* tab, TabDF tb) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    Pair p;
+    p.hi = __double2float_rn(x[i]);
+    p.lo = __double2float_rn(x[i] - (double)p.hi);
+    Pair ss, cc;
+    sincos_df(p, tab, tb, ss, cc);
+    s[i] = (double)ss.hi + (double)ss.lo;
+    c[i] = (double)cc.hi + (double)cc.lo;
+  }
+}
+
+}  // namespace
+
+void df_tab(TabDF* tb);
+
+cudaError_t launch_debug_sincos_df(const double* x, double* s, double* c, long long n, const float4* scd,
+                                   cudaStream_t st) {
+  TabDF tb;
+  df_tab(&tb);
+  long long g = (n + 255) / 256;
+  const int grid = (int)(g > 4096 ? 4096 : (g < 1 ? 1 : g));
+  k_debug_sincos_df<<<grid, 256, 0, st>>>(x, s, c, n, scd, tb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_iterate_df64(const IterArgs& a, int scheme, bool tangent, int block, int grid, cudaStream_t st) {
+  TabDF tb;
+  df_tab(&tb);
+  const CoefDF cf = coef_df(a.cf);
+  switch (scheme) {
+    case ARNOLD_SCHEME_YOSHIDA6A:
+      return tangent ? launch_one<7, true>(a, tb, cf, block, grid, st) : launch_one<7, false>(a, tb, cf, block, grid, st);
+    case ARNOLD_SCHEME_TRIPLEJUMP6:
+      return tangent ? launch_one<9, true>(a, tb, cf, block, grid, st) : launch_one<9, false>(a, tb, cf, block, grid, st);
+    case ARNOLD_SCHEME_LEAPFROG2:
+      return tangent ? launch_one<1, true>(a, tb, cf, block, grid, st) : launch_one<1, false>(a, tb, cf, block, grid, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int df64_blocks_per_sm(int scheme, bool tangent, int block) {
+  TabDF tb;
+  df_tab(&tb);
+  switch (scheme) {
+    case ARNOLD_SCHEME_YOSHIDA6A: return tangent ? occ_one<7, true>(tb, block) : occ_one<7, false>(tb, block);
+    case ARNOLD_SCHEME_TRIPLEJUMP6: return tangent ? occ_one<9, true>(tb, block) : occ_one<9, false>(tb, block);
+    default: return tangent ? occ_one<1, true>(tb, block) : occ_one<1, false>(tb, block);
+  }
+}
+
+}  // namespace arnold

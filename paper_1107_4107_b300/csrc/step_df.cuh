@@ -1,0 +1,189 @@
+// Double-float ("DF64") building blocks: FP64-grade arithmetic on the FP32
+// pipes.  A value is a float pair (hi, lo) with |lo| <= ulp(hi)/2 after
+// renormalisation (about 48 significant bits); products use the exact FMA
+// split (Dekker / Ogita-Rump-Oishi TwoProd) and sums Knuth's TwoSum, so each
+// operation is correct to ~2^-47 relative.  The B300 issues FP32 FMAs 74x
+// faster than FP64 ones, so the whole kick (sincos, force) in double-float
+// costs a fraction of the native FP64 kick.
+#pragma once
+#include "step32.cuh"
+
+namespace arnold {
+
+// Sincos table of the DF64 path: theta_j = 2 pi j / 2048, entry j holds
+// (sin hi, sin lo, cos hi, cos lo) rounded from long-double libm; the step
+// D = 2 pi / 2048 is split d1 (11 significant bits, so j d1 is exact for
+// |j| < 8192) + d2 + d3 (59 bits in all).  Angles are reduced every step, so
+// |x| <= 2 pi + h |q| and |j| < 8192 for h |q| < 9 per step.
+struct TabDF {
+  float inv_d, d1, d2, d3;
+  int mask;          // 2047
+  float inv2pi, c1, c2, c3;
+};
+
+__device__ __forceinline__ Pair df_mul(const Pair& a, const Pair& b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  Pair r;
+  fast_two_sum(p, e, r.hi, r.lo);
+  return r;
+}
+
+__device__ __forceinline__ Pair df_sqr(const Pair& a) {
+  const float p = __fmul_rn(a.hi, a.hi);
+  float e = fmaf(a.hi, a.hi, -p);
+  e = fmaf(2.0f * a.hi, a.lo, e);
+  Pair r;
+  fast_two_sum(p, e, r.hi, r.lo);
+  return r;
+}
+
+__device__ __forceinline__ Pair df_add(const Pair& a, const Pair& b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  Pair r;
+  fast_two_sum(s, e, r.hi, r.lo);
+  return r;
+}
+
+// x += inc (both pairs), keeping x's low word for the next renormalisation.
+__device__ __forceinline__ void df_acc(Pair& x, const Pair& inc) {
+  float s, e;
+  two_sum(x.hi, inc.hi, s, e);
+  x.hi = s;
+  x.lo = __fadd_rn(x.lo, __fadd_rn(e, inc.lo));
+}
+
+// sin and cos of the pair x to a few units of the pair's last place (~1e-14
+// for values near 1; Tang's table method in double-float): x = theta_j + r,
+// r formed exactly as a pair, sin r - r and
+// cos r - 1 from their Taylor terms (r^3/6, r^5/120 in FP32, r^2/2 as a pair,
+// r^4/24 in FP32; |r| <= 1.6e-3 so the next terms are < 1e-19), then
+// sin x = S + C (r + u) + S cm and cos x = C - S (r + u) + C cm with the large
+// products split exactly and the small ones gathered in FP32.
+__device__ __forceinline__ void sincos_df(const Pair& x, const float4* __restrict__ tab, const TabDF& tb, Pair& s,
+                                          Pair& c) {
+  const float t = fmaf(x.hi, tb.inv_d, 12582912.0f);
+  const float jf = __fsub_rn(t, 12582912.0f);
+  const int j = (__float_as_int(t) - 0x4B400000) & tb.mask;
+  const float r1 = fmaf(-jf, tb.d1, x.hi);                 // exact
+  const float p = __fmul_rn(jf, tb.d2);
+  const float pe = fmaf(jf, tb.d2, -p);                     // exact error of jf * d2
+  float a, ae, rh, be;
+  two_sum(r1, -p, a, ae);                                  // exact
+  two_sum(a, x.lo, rh, be);                                // exact: the low word joins before rounding
+  float rl = fmaf(-jf, tb.d3, __fadd_rn(be, __fsub_rn(ae, pe)));
+  fast_two_sum(rh, rl, rh, rl);
+  const float r2h = __fmul_rn(rh, rh);
+  const float r2e = fmaf(2.0f * rh, rl, fmaf(rh, rh, -r2h));
+  const float r3 = __fmul_rn(r2h, rh);
+  const float u = __fmul_rn(r3, fmaf(r2h, 1.0f / 120.0f, -1.0f / 6.0f));   // sin r - r
+  const float cmh = -0.5f * r2h;                                           // cos r - 1 (leading, exact)
+  const float cml = fmaf(__fmul_rn(r2h, r2h), 1.0f / 24.0f, -0.5f * r2e);
+  const float4 e = tab[j];   // (S hi, S lo, C hi, C lo)
+  const float rlu = __fadd_rn(rl, u);
+  {
+    const float pa = __fmul_rn(e.z, rh), ea = fmaf(e.z, rh, -pa);        // C_h r_h
+    const float pb = __fmul_rn(e.x, cmh), eb = fmaf(e.x, cmh, -pb);      // S_h cm_h
+    float s1, e1, s2, e2;
+    two_sum(e.x, pa, s1, e1);
+    two_sum(s1, pb, s2, e2);
+    float sm = __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(ea, eb));
+    sm = __fadd_rn(sm, e.y);
+    sm = fmaf(e.z, rlu, sm);
+    sm = fmaf(e.w, rh, sm);
+    sm = fmaf(e.x, cml, sm);
+    sm = fmaf(e.y, cmh, sm);
+    fast_two_sum(s2, sm, s.hi, s.lo);
+  }
+  {
+    const float pa = __fmul_rn(e.x, rh), ea = fmaf(e.x, rh, -pa);        // S_h r_h
+    const float pb = __fmul_rn(e.z, cmh), eb = fmaf(e.z, cmh, -pb);      // C_h cm_h
+    float c1, f1, c2, f2;
+    two_sum(e.z, -pa, c1, f1);
+    two_sum(c1, pb, c2, f2);
+    float sm = __fadd_rn(__fadd_rn(f1, f2), __fsub_rn(eb, ea));
+    sm = __fadd_rn(sm, e.w);
+    sm = fmaf(-e.x, rlu, sm);
+    sm = fmaf(-e.y, rh, sm);
+    sm = fmaf(e.z, cml, sm);
+    sm = fmaf(e.w, cmh, sm);
+    fast_two_sum(c2, sm, c.hi, c.lo);
+  }
+}
+
+// Kick in double-float: q_u += G s_u, q_v += G s_v, p_z += Sp A with
+// G = k2 c_z^2, Sp = k2 s_z c_z, A = c_u + c_v (k2 = 2 tau eps as a pair);
+// the tangent update uses the leading words in FP32 (as in the FP32C path).
+template <bool TAN>
+__device__ __forceinline__ void kick_df(Traj32& t, const Pair& k2, float k4f, const float4* tab, const TabDF& tb) {
+  Pair su, cu, sv, cv, sz, cz;
+  sincos_df(t.u, tab, tb, su, cu);
+  sincos_df(t.v, tab, tb, sv, cv);
+  sincos_df(t.z, tab, tb, sz, cz);
+  const Pair g = df_sqr(cz);
+  const Pair sh = df_mul(sz, cz);
+  const Pair G = df_mul(k2, g);
+  const Pair Sp = df_mul(k2, sh);
+  const Pair A = df_add(cu, cv);
+  df_acc(t.qu, df_mul(G, su));
+  df_acc(t.qv, df_mul(G, sv));
+  df_acc(t.pz, df_mul(Sp, A));
+  if (TAN) {
+    const float Gf = G.hi, Spf = Sp.hi, Af = A.hi, gf = g.hi, k2f = k2.hi;
+    const float Gu = Gf * cu.hi, Gv = Gf * cv.hi;
+    const float Yu = Spf * su.hi, Yv = Spf * sv.hi;
+    const float Z = Af * fmaf(k4f, gf, -k2f);
+    const float m2dz = -2.0f * t.dz;
+    t.dqu = fmaf(Gu, t.du, t.dqu);
+    t.dqu = fmaf(Yu, m2dz, t.dqu);
+    t.dqv = fmaf(Gv, t.dv, t.dqv);
+    t.dqv = fmaf(Yv, m2dz, t.dqv);
+    t.dpz = fmaf(Z, t.dz, t.dpz);
+    t.dpz = fmaf(-Yu, t.du, t.dpz);
+    t.dpz = fmaf(-Yv, t.dv, t.dpz);
+  }
+}
+
+// Potential (Eq. 2) in double-float, returned as FP64.
+__device__ __forceinline__ double potential_df(const Traj32& t, const float4* tab, const TabDF& tb) {
+  Pair su, cu, sv, cv, sz, cz;
+  sincos_df(t.u, tab, tb, su, cu);
+  sincos_df(t.v, tab, tb, sv, cv);
+  sincos_df(t.z, tab, tb, sz, cz);
+  const double A = ((double)cu.hi + (double)cu.lo) + ((double)cv.hi + (double)cv.lo);
+  const double c = (double)cz.hi + (double)cz.lo;
+  return A * (c * c);
+}
+
+}  // namespace arnold
+
+namespace arnold {
+
+// End of a DF64 step: renormalise every pair and remove whole turns from the
+// angles (exactly, 2 pi as three floats), every step, so that each kick's
+// argument stays within the table's exact index range.
+__device__ __forceinline__ void reduce_angle_df(Pair& x, int& lap, const TabDF& tb) {
+  const float t = fmaf(x.hi, tb.inv2pi, 12582912.0f);
+  const float kf = __fsub_rn(t, 12582912.0f);
+  const int k = __float_as_int(t) - 0x4B400000;
+  const float h1 = fmaf(-kf, tb.c1, x.hi);
+  float s, e;
+  two_sum(h1, __fmul_rn(-kf, tb.c2), s, e);
+  const float lo = fmaf(-kf, tb.c3, __fadd_rn(x.lo, e));
+  fast_two_sum(s, lo, x.hi, x.lo);
+  lap += k;
+}
+
+__device__ __forceinline__ void end_step_df(Traj32& t, const TabDF& tb) {
+  renorm(t.qu); renorm(t.qv); renorm(t.pz);
+  renorm(t.u); renorm(t.v); renorm(t.z);
+  reduce_angle_df(t.u, t.lu, tb);
+  reduce_angle_df(t.v, t.lv, tb);
+  reduce_angle_df(t.z, t.lz, tb);
+}
+
+}  // namespace arnold

@@ -1,0 +1,119 @@
+"""DF64 path (double-float state and kicks on the FP32 pipes) against the FP64
+oracle at the FP64 tolerance.
+
+A double-float word carries ~48 significant bits against FP64's 53, so every
+rounding (and the initial conversion of the state) is ~2^5 = 32 times coarser
+than in the FP64 kernel; the trajectory (displacement, momenta, V) is held to
+the FP64 bound scaled by that factor, 3e-11 relative (measured ~2e-12 over
+1000 steps).  The tangent vector is FP32 in this mode, so the FTLE is held to
+the FP32C bounds.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1107_4107_b300 import inputs
+from parity import oracle_grid_state, oracle_params, rel_err
+
+pytestmark = pytest.mark.gpu
+TOL = 3e-11
+
+
+def _ens(n, **kw):
+    from paper_1107_4107_b300.api import ArnoldEnsemble
+    return ArnoldEnsemble(n, precision="df64", **kw)
+
+
+def test_df64_sincos_accuracy():
+    import torch
+    # inputs exactly representable as float pairs (hi + lo), so the test sees the
+    # sincos error and not the 48-bit rounding of the argument
+    x0 = np.linspace(0.0, 2 * math.pi, 400001)
+    hi = x0.astype(np.float32)
+    lo = (x0 - hi.astype(np.float64)).astype(np.float32)
+    x = hi.astype(np.float64) + lo.astype(np.float64)
+    xd = torch.tensor(x, device="cuda")
+    s = torch.empty_like(xd)
+    c = torch.empty_like(xd)
+    e = _ens(8)
+    e.debug_sincos(xd, s, c, "df64")
+    es = np.abs(s.cpu().numpy() - np.sin(x)).max()
+    ec = np.abs(c.cpu().numpy() - np.cos(x)).max()
+    # a float pair resolves ~2^-48 relative: a few of its last places ~ 1e-14
+    assert es < 2e-14 and ec < 2e-14, (es, ec)
+
+
+@pytest.mark.parametrize("n", [33, 1000])
+def test_df64_state_parity_all_cells(n):
+    X, P = inputs.box(n, seed=41)
+    st = oracle.State(X, P, oracle_params(R=10))
+    e = _ens(n, renorm_every=10)
+    e.set_state(X, P)
+    for S in (1, 9, 90):
+        e.iterate(S)
+        st.advance(S)
+        assert rel_err(e.indicator("dX"), st.unwrapped_displacement()) < TOL
+        assert rel_err(e.indicator("P"), st.P) < TOL
+    assert rel_err(e.indicator("V"), st.velocity()) < TOL
+    assert rel_err(e.indicator("chi"), st.chi()) < 1e-6
+    assert np.max(np.abs(e.indicator("dE_max") - st.dE_max)) < 1e-9
+
+
+def test_df64_long_horizon_low_growth_cells():
+    n = 1024
+    X, P = inputs.box(n, seed=42)
+    st = oracle.State(X, P, oracle_params()).advance(1000, threads=4)
+    e = _ens(n)
+    e.set_state(X, P)
+    e.iterate(1000)
+    low = st.chi() * st.time() < 5.0
+    assert low.mean() > 0.3
+    for kind, ref in (("dX", st.unwrapped_displacement()), ("P", st.P)):
+        assert rel_err(e.indicator(kind)[:, low], ref[:, low]) < TOL, kind
+    assert np.array_equal(e.indicator("class")[low], st.classify()[low])
+
+
+@pytest.mark.parametrize("E", [400.0, 40.0])
+def test_df64_grid_parity(E):
+    G = 32
+    st = oracle_grid_state(G, E, oracle_params())
+    e = _ens(G * G)
+    e.init_grid(G, E)
+    e.iterate(100)
+    st.advance(100, threads=4)
+    assert rel_err(e.indicator("dX"), st.unwrapped_displacement()) < TOL
+    assert rel_err(e.indicator("P"), st.P) < TOL
+
+
+def test_df64_range_is_reported():
+    """h |q| beyond the table's exact range is reported as ERANGE, not computed wrong."""
+    from paper_1107_4107_b300._lib import ArnoldError, ERANGE
+    X, P = inputs.box(64, seed=1, lo=(300.0, 300.0, 300.0), hi=(301.0, 301.0, 301.0))
+    e = _ens(64, h=0.1, renorm_every=1)
+    e.set_state(X, P)
+    e.iterate(2)
+    with pytest.raises(ArnoldError) as ex:
+        e.sync()
+    assert ex.value.status == ERANGE
+
+
+def test_df64_resume_bitwise_and_no_adjoint():
+    from paper_1107_4107_b300._lib import ArnoldError, EUNSUPPORTED
+    X, P = inputs.box(500, seed=5)
+    ref = _ens(500, renorm_every=7)
+    ref.set_state(X, P)
+    ref.iterate(120)
+    a = _ens(500, renorm_every=7)
+    a.set_state(X, P)
+    a.iterate(50)
+    blob = a.checkpoint()
+    b = _ens(500, renorm_every=7)
+    b.restore(blob)
+    b.iterate(70)
+    for k in ("dX", "P", "tangent", "chi"):
+        assert np.array_equal(ref.indicator(k), b.indicator(k)), k
+    with pytest.raises(ArnoldError) as ex:
+        b.forward_ckpt(10)
+    assert ex.value.status == EUNSUPPORTED
