@@ -293,35 +293,17 @@ def main():
                "steps": k2, "api": "ArnoldEnsemble.set_state/iterate/indicator (C ABI, host pinned buffers)"}
         ens2.close()
 
-    # ---- FP32C (compensated) on the same workload ----
+    # ---- FP32C and DF64 on the same grid, to the same step count, compared with FP64 ----
+    fp64_steps = ens.steps
+    chi64 = ens.indicator("chi")
+    cls64 = ens.indicator("class")
     fp32c = None
+    df64 = None
     if not args.no_fp32c:
-        e3 = ArnoldEnsemble(n, precision="fp32c", device=local, stream=stream.cuda_stream)
-        e3.init_grid(G, E, seed=rank)
-        ch32 = args.chunk * 20
-        e3.iterate(ch32)
-        barrier()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        k3 = max(2, args.steps // 2)
-        a.record(stream)
-        for _ in range(k3):
-            e3.iterate(ch32)
-        b.record(stream)
-        barrier()
-        ms3 = a.elapsed_time(b)
-        v3 = n * ch32 * k3 / (ms3 * 1e-3)
-        fp32c = {"value": v3, "unit": "map-steps/s", "speedup_vs_fp64": v3 / (value / world),
-                 "steps_per_bench_step": ch32, "steps": k3,
-                 "roofline": {"bound": "alu", "kernel": "k_iterate_fp32c<7,true,false>",
-                              "achieved_instr_per_s": v3 * FP32C_INSTR_PER_STEP, "peak_instr_per_s": ffma,
-                              "frac": v3 * FP32C_INSTR_PER_STEP / ffma,
-                              "issue_frac": v3 * FP32C_ISSUED_PER_STEP_NCU / ffma,
-                              "peak_source": "measured live: FFMA probe (1 warp instruction / clock / SMSP = the "
-                                             "issue peak)", "instr_per_map_step": FP32C_INSTR_PER_STEP,
-                              "issued_instr_per_map_step_ncu": FP32C_ISSUED_PER_STEP_NCU},
-                 "agreement_note": "class agreement and histogram L1 vs FP64 are checked in tests/test_gpu_fp32c.py"}
-        e3.close()
+        fp32c = precision_leg("fp32c", n, rank, local, stream, barrier, fp64_steps, chi64, cls64, value / world,
+                              ffma, FP32C_INSTR_PER_STEP, FP32C_ISSUED_PER_STEP_NCU)
+        df64 = precision_leg("df64", n, rank, local, stream, barrier, fp64_steps, chi64, cls64, value / world,
+                             ffma, None, None)
 
     adjoint = None if args.no_extras else adjoint_leg(stream, local, barrier)
     batch = None if args.no_extras else batch_leg(stream, local, barrier, args)
@@ -335,11 +317,58 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(args),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(gpu_launches),
-            "clocks": clk.summary(), "fp32c": fp32c, "adjoint": adjoint, "batch": batch,
+            "clocks": clk.summary(), "fp32c": fp32c, "df64": df64, "adjoint": adjoint, "batch": batch,
             "probe": {"dfma_per_s": dfma, "ffma_per_s": ffma}}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def hist_l1(a, b):
+    """L1 distance of the normalised histograms of log10 chi (200 bins on [-8, 1])."""
+    ha, _ = np.histogram(np.log10(np.clip(a, 1e-300, None)), bins=200, range=(-8, 1))
+    hb, _ = np.histogram(np.log10(np.clip(b, 1e-300, None)), bins=200, range=(-8, 1))
+    return float(np.abs(ha / len(a) - hb / len(b)).sum())
+
+
+def precision_leg(prec, n, rank, device, stream, barrier, steps, chi64, cls64, fp64_rate, ffma, instr, issued):
+    """The same 2048 x 2048 scan in another precision mode, run to the FP64 scan's
+    step count from the same initial conditions: throughput, and agreement of
+    the regular/chaotic classes and of the log10 chi histograms with FP64."""
+    import torch
+    from paper_1107_4107_b300.api import ArnoldEnsemble
+    w = ArnoldEnsemble(2048, precision=prec, device=device, stream=stream.cuda_stream)
+    w.init_grid(2048, E, seed=rank, row0=7)
+    w.iterate(20)
+    w.close()
+    e = ArnoldEnsemble(n, precision=prec, device=device, stream=stream.cuda_stream)
+    e.init_grid(G, E, seed=rank)
+    barrier()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    e.iterate(steps)
+    b.record(stream)
+    barrier()
+    ms = a.elapsed_time(b)
+    v = n * steps / (ms * 1e-3)
+    chi = e.indicator("chi")
+    cls = e.indicator("class")
+    out = {"value": v, "unit": "map-steps/s", "speedup_vs_fp64": v / fp64_rate, "steps": steps,
+           "class_agreement_vs_fp64": float(np.mean(cls == cls64)), "hist_l1_vs_fp64": hist_l1(chi, chi64),
+           "chaotic_fraction": float(np.mean(cls)), "chaotic_fraction_fp64": float(np.mean(cls64)),
+           "agreement_note": "at this horizon few or no cells pass the chaos threshold, so the class agreement is "
+                             "near-trivial; the chi histogram L1 is the informative figure (1e4-step agreement is "
+                             "tested in tests/test_gpu_fp32c.py)"}
+    if instr is not None:
+        out["roofline"] = {"bound": "alu", "kernel": "k_iterate_fp32c<7,true,false>",
+                           "achieved_instr_per_s": v * instr, "peak_instr_per_s": ffma, "frac": v * instr / ffma,
+                           "issue_frac": v * issued / ffma,
+                           "peak_source": "measured live: FFMA probe (1 warp instruction / clock / SMSP = the "
+                                          "issue peak)", "instr_per_map_step": instr,
+                           "issued_instr_per_map_step_ncu": issued}
+    e.close()
+    return out
 
 
 def adjoint_leg(stream, device, barrier):
