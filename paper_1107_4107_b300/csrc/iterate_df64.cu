@@ -20,11 +20,16 @@ struct CoefDF {
   float k4f[9];
 };
 
+// The substep loop is not unrolled: a double-float kick is ~350 instructions,
+// and seven unrolled copies overflow the instruction cache (ncu: issue stalls
+// on instruction fetch); the loop reads its coefficients from shared memory.
 template <int M, bool TAN>
-__global__ void __launch_bounds__(256) k_iterate_df64(IterArgs a, TabDF tb, CoefDF cf) {
+__global__ void __launch_bounds__(256) k_iterate_df64(IterArgs a, TabDF tb, CoefDF cfg) {
   extern __shared__ __align__(16) unsigned char smem[];
   float4* stab = reinterpret_cast<float4*>(smem);
+  __shared__ CoefDF cf;
   for (int k = threadIdx.x; k <= tb.mask; k += blockDim.x) stab[k] = a.scd[k];
+  if (threadIdx.x == 0) cf = cfg;
   __syncthreads();
   RunArgs32 ra;
   ra.s = a.s;
@@ -47,7 +52,7 @@ __global__ void __launch_bounds__(256) k_iterate_df64(IterArgs a, TabDF tb, Coef
 #pragma unroll 1
     for (int s = 0; s < a.nsteps; ++s) {
       drift32<TAN>(t, cf.sh[0], cf.sl[0]);
-#pragma unroll
+#pragma unroll 1
       for (int k = 0; k < M; ++k) {
         kick_df<TAN>(t, cf.k2[k], cf.k4f[k], stab, tb);
         drift32<TAN>(t, cf.sh[k + 1], cf.sl[k + 1]);
@@ -68,7 +73,7 @@ __global__ void __launch_bounds__(256) k_iterate_df64(IterArgs a, TabDF tb, Coef
         const double dE = fabs(kin + a.eps * potential_df(t, stab, tb) - a.s.e0[i]);
         demax = fmax(demax, dE);
         if (!isfinite(dE)) bad = 1;
-        // the table's exact index range needs |angle| < 12.5 inside a step
+        // the table's exact index range needs |angle| < 25 inside a step
         const float qmax = fmaxf(fmaxf(fabsf(t.qu.hi), fabsf(t.qv.hi)), fabsf(t.pz.hi));
         if (qmax * fabsf(hf) > 9.0f) atomicOr(a.flags, kFlagRange);
         if (a.s.left) {
