@@ -62,7 +62,7 @@ def lib():
         dp = ctypes.POINTER(ctypes.c_double)
         ip = ctypes.POINTER(ctypes.c_int64)
         L.oracle_run.argtypes = [ctypes.POINTER(_Params), ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
-                                 dp, dp, dp, ip, dp, dp, dp, dp, dp]
+                                 dp, dp, dp, ip, dp, dp, dp, dp, dp, dp]
         L.oracle_run.restype = ctypes.c_int
         L.oracle_energy.argtypes = [ctypes.c_double, ctypes.c_int64, dp, dp, dp]
         L.oracle_pz_from_energy.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int64, dp, dp]
@@ -218,6 +218,7 @@ class State:
         self.dE_max = np.zeros(n)
         self.e0 = energy(params.eps, self.X, self.P)
         self.V = np.zeros((3, n))
+        self.megno = np.zeros((2, n)) if tangent else None   # (S, Ysum), see megno_mean()
         self.steps = 0
 
     def run(self, n_steps: int, lo: int = 0, hi: int | None = None) -> "State":
@@ -236,9 +237,10 @@ class State:
         dE = np.ascontiguousarray(self.dE_max[sl])
         e0 = np.ascontiguousarray(self.e0[sl])
         V = np.ascontiguousarray(self.V[:, sl])
+        mg = None if self.megno is None else np.ascontiguousarray(self.megno[:, sl])
         rc = lib().oracle_run(ctypes.byref(self.params.c()), hi - lo, self.steps, n_steps,
                               _ptr(X), _ptr(P), _ptr(W), _ptr(lap), _ptr(xref), _ptr(logsum),
-                              _ptr(dE), _ptr(e0), _ptr(V))
+                              _ptr(dE), _ptr(e0), _ptr(V), _ptr(mg))
         if rc != 0:
             raise ValueError("oracle_run rejected its arguments")
         self.X[:, sl] = X
@@ -250,6 +252,8 @@ class State:
         self.logsum[sl] = logsum
         self.dE_max[sl] = dE
         self.V[:, sl] = V
+        if mg is not None:
+            self.megno[:, sl] = mg
         return self
 
     def advance(self, n_steps: int, threads: int = 1) -> "State":
@@ -275,6 +279,21 @@ class State:
     def chi(self) -> np.ndarray:
         """FTLE chi_t = (sum of renormalisation logs + ln|w|) / t."""
         return (self.logsum + np.log(np.sqrt(np.sum(self.W * self.W, axis=0)))) / self.time()
+
+    def renorm_count(self) -> int:
+        """Renormalisations so far (the MEGNO sample index m)."""
+        return self.steps // self.params.renorm_every
+
+    def megno_y(self) -> np.ndarray:
+        """MEGNO Y_m = (2/m) sum_j j l_j at the last renormalisation (0 before the first)."""
+        m = self.renorm_count()
+        return 2.0 * self.megno[0] / m if m else np.zeros(self.n)
+
+    def megno_mean(self) -> np.ndarray:
+        """Mean MEGNO <Y>_m = (1/m) sum_k Y_k: tends to 0 on stable periodic orbits, to 2 on
+        quasi-periodic ones (linear tangent growth), grows like lambda t / 2 on chaotic ones."""
+        m = self.renorm_count()
+        return self.megno[1] / m if m else np.zeros(self.n)
 
     def velocity(self) -> np.ndarray:
         """Finite-time averaged velocity V = [X(t+dt) - X(t)] / dt (Sec. IV)."""

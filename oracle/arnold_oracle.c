@@ -29,11 +29,25 @@
  *   D(s): dX += s dP;   K(t): dP -= t eps Hess Hp(X) dX  (Hessian at the kick's X).
  *   Every R steps (global step index multiple of R): l = |w|, logsum += ln l, w /= l.
  *
+ * MEGNO (the mean exponential growth factor of nearby orbits; Cincotta and
+ * Simo, Astron. Astrophys. Suppl. 147 (2000) 205; for maps Cincotta, Giordano
+ * and Simo, Physica D 182 (2003) 151) -- not in the paper, an alternative
+ * tangent-based indicator.  Its continuous definitions are
+ *   Y(t) = (2/t) int_0^t s d ln|w(s)|,   <Y>(t) = (1/t) int_0^t Y(s) ds.
+ * Sampled at the renormalisation points t_j = j R h (j = 1, 2, ... counted from
+ * the start of the run) with the increment over (t_{j-1}, t_j] taken at its
+ * right end, as the map form does: with l_j = ln of the norm growth over
+ * interval j,  Y_m = (2/m) sum_{j<=m} j l_j  and  <Y>_m = (1/m) sum_{k<=m} Y_k.
+ * Accumulated per trajectory: S_m = sum_{j<=m} j l_j and Ysum_m = sum_{k<=m} Y_k.
+ *
  * Parity: pinned (see tests/test_oracle_pins.py) by the free-rotation closed
  * form at eps = 0, the Chirikov standard map on an invariant subspace, the
  * pendulum period on that subspace, invariant subspaces, sixth-order
  * convergence, symplecticity of the tangent map, reversibility, and central
- * finite differences.
+ * finite differences; MEGNO (tests/test_oracle_megno.py) by the free-flow
+ * closed form of the tangent norm, its limits 0 (stable equilibrium), 2
+ * (linear growth) and lambda t / 2 (chaos), and the summation-by-parts
+ * identity against the log-sum history.
  */
 #include <math.h>
 #include <stdint.h>
@@ -122,6 +136,8 @@ typedef struct {
   double w[6];          /* tangent (dX, dP) */
   int64_t lap[3];       /* laps since the window started */
   double logsum;
+  double mg_s;          /* MEGNO: sum over renormalisations j of j * ln(growth) */
+  double mg_y;          /* MEGNO: sum over renormalisations of Y_j              */
   double dE_max;
   double e0;
   double xref[3];       /* reduced angle at the window start */
@@ -183,6 +199,9 @@ static void end_of_step(traj* t, const oracle_params* prm, int64_t step, int tan
       double l = norm6(t->w);
       t->logsum += log(l);
       for (int k = 0; k < 6; k++) t->w[k] /= l;
+      double j = (double)(step / prm->renorm_every);   /* index of this renormalisation */
+      t->mg_s += j * log(l);
+      t->mg_y += 2.0 * t->mg_s / j;
     }
     double dE = fabs(oracle_energy1(prm->eps, t->X, t->P) - t->e0);
     if (dE > t->dE_max) t->dE_max = dE;
@@ -207,11 +226,12 @@ static void end_of_step(traj* t, const oracle_params* prm, int64_t step, int tan
  *   xref[3][n]           reduced angle at the window start
  *   logsum[n], dE_max[n], e0[n]  (logsum may be NULL when W is NULL)
  *   V[3][n] or NULL      V of the last closed window (written when a window closes)
+ *   megno[2][n] or NULL  MEGNO sums (S, Ysum) over the renormalisations so far
  * Returns 0, or -1 on a bad argument.
  */
 int oracle_run(const oracle_params* prm, int64_t n, int64_t step0, int64_t n_steps,
                double* X, double* P, double* W, int64_t* lap, double* xref,
-               double* logsum, double* dE_max, const double* e0, double* V) {
+               double* logsum, double* dE_max, const double* e0, double* V, double* megno) {
   double wts[9];
   int m = oracle_scheme_weights(prm->scheme, wts);
   if (m < 0 || n < 0 || n_steps < 0 || prm->renorm_every < 1 || prm->window < 0) return -1;
@@ -229,6 +249,8 @@ int oracle_run(const oracle_params* prm, int64_t n, int64_t step0, int64_t n_ste
     if (tangent)
       for (int k = 0; k < 6; k++) t.w[k] = W[k * n + i];
     t.logsum = logsum ? logsum[i] : 0.0;
+    t.mg_s = megno ? megno[i] : 0.0;
+    t.mg_y = megno ? megno[n + i] : 0.0;
     t.dE_max = dE_max[i];
     t.e0 = e0[i];
     for (int64_t s = 0; s < n_steps; s++) {
@@ -245,6 +267,10 @@ int oracle_run(const oracle_params* prm, int64_t n, int64_t step0, int64_t n_ste
     if (tangent)
       for (int k = 0; k < 6; k++) W[k * n + i] = t.w[k];
     if (logsum) logsum[i] = t.logsum;
+    if (megno) {
+      megno[i] = t.mg_s;
+      megno[n + i] = t.mg_y;
+    }
     dE_max[i] = t.dE_max;
   }
   return 0;
