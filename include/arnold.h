@@ -77,6 +77,16 @@ extern "C" {
 #define ARNOLD_IND_TANGENT  8  /* [6][n] f64: (dx, dy, dz, dp_x, dp_y, dp_z), as renormalised             */
 #define ARNOLD_IND_LOGSUM   9  /* [n] f64: sum of ln|w| taken at renormalisations                        */
 #define ARNOLD_IND_LEFT    10  /* [n] u8: 1 if the momentum direction left the tracked patch (area filter) */
+/* MEGNO (mean exponential growth factor of nearby orbits; Cincotta & Simo,
+ * Astron. Astrophys. Suppl. 147 (2000) 205) -- not in the paper, a second
+ * tangent-based indicator beside chi.  Sampled at the m = steps / R
+ * renormalisations so far, l_j the log growth of |w| over interval j:
+ * Y_m = (2/m) sum_j j l_j and <Y>_m = (1/m) sum_{k<=m} Y_k.  <Y> tends to 0 on
+ * stable periodic orbits, to 2 on quasi-periodic ones and grows like
+ * lambda t / 2 on chaotic ones.  Both read 0 before the first renormalisation.
+ * Needs a context created with megno = 1 (EINVAL otherwise). */
+#define ARNOLD_IND_MEGNO   11  /* [n] f64: mean MEGNO <Y>_m                                              */
+#define ARNOLD_IND_MEGNO_Y 12  /* [n] f64: MEGNO Y_m at the last renormalisation                         */
 
 /* ---- parameters ------------------------------------------------------------ */
 typedef struct arnold_params {
@@ -90,6 +100,8 @@ typedef struct arnold_params {
   double  chaos_kappa;   /* kappa > 0 of the regular/chaotic threshold (default 10)         */
   int32_t block_size;    /* threads per block, multiple of 32 in [32, 256]; 0 = default    */
   int32_t launch_steps;  /* max composite steps per kernel launch; 0 = automatic (~0.2 s)   */
+  int32_t megno;         /* 1: also accumulate MEGNO (needs tangent = 1); 0: off            */
+  int32_t reserved;      /* must be 0                                                       */
 } arnold_params;
 
 /* Fill defaults: eps 1, h 0.02 pi, Yoshida-6A, FP64, tangent on, R 100,
@@ -301,16 +313,16 @@ void arnold_batch_destroy(arnold_batch* b);
 
 /* ---- checkpoint / resume ----------------------------------------------------
  * The complete per-trajectory state (phase-space state, tangent, laps, window
- * references, log sums, energy references and maxima, V) plus the step
- * counter, so that a run resumed from a checkpoint continues bit for bit as
- * if uninterrupted (the paper's 24 h runs, Sec. IV, motivate it).  Layout: a
- * 64-byte header (magic "ARNOLDC1", precision, tangent, n, steps, scheme,
- * eps, h) followed by the device arrays.  The buffer is host memory owned by
+ * references, log sums, energy references and maxima, V, MEGNO sums when
+ * enabled) plus the step counter, so that a run resumed from a checkpoint
+ * continues bit for bit as if uninterrupted (the paper's 24 h runs, Sec. IV,
+ * motivate it).  Layout: a 64-byte header (magic "ARNOLDC1", precision,
+ * tangent, n, steps, scheme, megno, eps, h) followed by the device arrays.  The buffer is host memory owned by
  * the caller. */
 int arnold_checkpoint_size(const arnold_ctx* ctx, size_t* bytes);
 /* Synchronises.  Errors: EINVAL (NULL, bytes too small), ECUDA. */
 int arnold_checkpoint_save(arnold_ctx* ctx, void* host_buf, size_t bytes);
-/* The context must have the same n, precision, tangent, scheme, eps and h.
+/* The context must have the same n, precision, tangent, scheme, megno, eps and h.
  * Errors: EINVAL (mismatch, bad magic, size), ECUDA. */
 int arnold_checkpoint_load(arnold_ctx* ctx, const void* host_buf, size_t bytes);
 

@@ -43,12 +43,13 @@ class ArnoldEnsemble:
 
     def __init__(self, n: int, eps: float = 1.0, h: float | None = None, scheme: str = "yoshida6a",
                  precision: str = "fp64", tangent: bool = True, renorm_every: int = 100, window: int = 0,
-                 kappa: float = 10.0, device: int = 0, stream=None, block_size: int = 0, launch_steps: int = 0):
+                 kappa: float = 10.0, device: int = 0, stream=None, block_size: int = 0, launch_steps: int = 0,
+                 megno: bool = False):
         L = _lib.lib()
         self.n = int(n)
         self.params = _lib.Params(eps, paper_h() if h is None else h, _lib.SCHEMES[scheme],
                                   _lib.PRECISIONS[precision], int(bool(tangent)), renorm_every, window, kappa,
-                                  block_size, launch_steps)
+                                  block_size, launch_steps, int(bool(megno)), 0)
         if stream is None:
             stream_ptr = None
             try:

@@ -123,6 +123,8 @@ int cuda_status(cudaError_t e) {
     if (_e != cudaSuccess) return cuda_status(_e);     \
   } while (0)
 
+static_assert(sizeof(arnold_params) == 64, "arnold_params layout is part of the ABI");
+
 int params_ok(const arnold_params* p) {
   if (!p) return 0;
   if (!(p->h != 0.0) || !isfinite(p->h) || !isfinite(p->eps)) return 0;
@@ -133,6 +135,9 @@ int params_ok(const arnold_params* p) {
   if (!(p->chaos_kappa > 0.0)) return 0;
   if (p->block_size != 0 && (p->block_size < 32 || p->block_size > 256 || p->block_size % 32)) return 0;
   if (p->launch_steps < 0) return 0;
+  if (p->megno != 0 && p->megno != 1) return 0;
+  if (p->megno && !p->tangent) return 0;
+  if (p->reserved != 0) return 0;
   return 1;
 }
 
@@ -246,7 +251,7 @@ void free_all(arnold_ctx* c) {
   void* ptrs[] = {c->s.st, c->s.tg, c->s.lap, c->s.lapref, c->s.ref, c->s.logsum, c->s.demax, c->s.e0, c->s.V,
                   c->f.hi, c->f.lo, c->f.tg, c->sc, c->th, c->scf, c->scd, c->flags, c->partials, c->stats_out,
                   c->scratch, c->scratch2, c->ck, c->seg, c->lam, c->lamf, c->gh, c->ge, c->sum_part, c->s.left,
-                  c->vhist};
+                  c->vhist, c->s.megno};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -302,6 +307,7 @@ int read_indicator(arnold_ctx* c, int kind, void* dst) {
   r.eps = c->prm.eps;
   const double tt = fabs(r.t);
   r.threshold = c->prm.chaos_kappa * log(tt > M_E ? tt : M_E) / tt;
+  r.m = c->steps / c->prm.renorm_every;
   r.out = dst;
   ACHECK(launch_indicator(r, grid_for(c, 256), 256, c->stream));
   c->launches++;
@@ -310,7 +316,8 @@ int read_indicator(arnold_ctx* c, int kind, void* dst) {
 
 size_t indicator_bytes(int kind, long long n) {
   switch (kind) {
-    case ARNOLD_IND_CHI: case ARNOLD_IND_DE: case ARNOLD_IND_DE_MAX: case ARNOLD_IND_LOGSUM: return 8 * (size_t)n;
+    case ARNOLD_IND_CHI: case ARNOLD_IND_DE: case ARNOLD_IND_DE_MAX: case ARNOLD_IND_LOGSUM:
+    case ARNOLD_IND_MEGNO: case ARNOLD_IND_MEGNO_Y: return 8 * (size_t)n;
     case ARNOLD_IND_CLASS: case ARNOLD_IND_LEFT: return (size_t)n;
     case ARNOLD_IND_V: case ARNOLD_IND_X: case ARNOLD_IND_P: case ARNOLD_IND_DX: return 24 * (size_t)n;
     case ARNOLD_IND_TANGENT: return 48 * (size_t)n;
@@ -403,6 +410,7 @@ int arnold_create(const arnold_params* prm, int64_t n_traj, int device, void* cu
   if (e == cudaSuccess) e = dalloc(&c->s.lapref, 3 * n);
   if (e == cudaSuccess) e = dalloc(&c->s.ref, 3 * n);
   if (e == cudaSuccess && tan) e = dalloc(&c->s.logsum, n);
+  if (e == cudaSuccess && prm->megno) e = dalloc(&c->s.megno, 2 * n);
   if (e == cudaSuccess) e = dalloc(&c->s.demax, n);
   if (e == cudaSuccess) e = dalloc(&c->s.e0, n);
   if (e == cudaSuccess) e = dalloc(&c->s.V, 3 * n);
@@ -620,6 +628,7 @@ int arnold_indicator(arnold_ctx* c, int kind, void* out, int ptr_kind) {
   const bool needs_tan = kind == ARNOLD_IND_CHI || kind == ARNOLD_IND_CLASS || kind == ARNOLD_IND_LOGSUM ||
                          kind == ARNOLD_IND_TANGENT;
   if (needs_tan && !c->prm.tangent) return ARNOLD_EINVAL;
+  if ((kind == ARNOLD_IND_MEGNO || kind == ARNOLD_IND_MEGNO_Y) && !c->s.megno) return ARNOLD_EINVAL;
   if (fault_is("nan")) return ARNOLD_ENONFINITE;
   ACHECK(cudaSetDevice(c->device));
   if (ptr_kind == ARNOLD_DEVICE) return read_indicator(c, kind, out);
@@ -815,7 +824,7 @@ struct CkptHeader {
   char magic[8];
   int32_t precision, tangent;
   int64_t n, steps;
-  int32_t scheme, pad;
+  int32_t scheme, megno;
   double eps, h;
   int64_t reserved;
 };
@@ -840,6 +849,7 @@ static int ckpt_arrays(const arnold_ctx* c, void** ptrs, size_t* sizes) {
   add(c->s.demax, 8 * n);
   add(c->s.e0, 8 * n);
   add(c->s.V, 24 * n);
+  add(c->s.megno, 16 * n);
   return k;
 }
 
@@ -866,6 +876,7 @@ int arnold_checkpoint_save(arnold_ctx* c, void* buf, size_t bytes) {
   hd.n = c->n;
   hd.steps = c->steps;
   hd.scheme = c->prm.scheme;
+  hd.megno = c->prm.megno;
   hd.eps = c->prm.eps;
   hd.h = c->prm.h;
   memcpy(buf, &hd, sizeof hd);
@@ -887,7 +898,7 @@ int arnold_checkpoint_load(arnold_ctx* c, const void* buf, size_t bytes) {
   CkptHeader hd;
   memcpy(&hd, buf, sizeof hd);
   if (memcmp(hd.magic, "ARNOLDC1", 8) || hd.precision != c->prm.precision || hd.tangent != c->prm.tangent ||
-      hd.n != c->n || hd.scheme != c->prm.scheme || hd.eps != c->prm.eps || hd.h != c->prm.h || hd.steps < 0)
+      hd.n != c->n || hd.scheme != c->prm.scheme || hd.megno != c->prm.megno || hd.eps != c->prm.eps || hd.h != c->prm.h || hd.steps < 0)
     return ARNOLD_EINVAL;
   ACHECK(cudaSetDevice(c->device));
   void* p[16];

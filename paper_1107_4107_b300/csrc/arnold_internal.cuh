@@ -58,7 +58,19 @@ struct Fp64State {
   double* V;       // [3][n] V (x, y, z components) of the last closed window
   unsigned char* left;  // [n] area tracking: 1 once the momentum direction left the patch (null = off)
   double patch[4];      // cos_lo, cos_hi, phi_lo, phi_hi of the tracked patch
+  double* megno;        // [2][n] MEGNO sums S = sum_j j l_j and Ysum = sum_j Y_j (null = off)
 };
+
+// MEGNO (Cincotta & Simo 2000) sampled at the renormalisation points: at the
+// j-th renormalisation (j counted from the start of the run) with log growth
+// l over the interval, S += j l and Ysum += Y_j = 2 S / j.  Read-modify-write
+// in HBM once per renormalisation interval, so nothing stays live in the step.
+__device__ __forceinline__ void megno_update(double* mg, long long n, long long i, long long j, double l) {
+  const double jd = (double)j;
+  const double S = mg[i] + jd * l;
+  mg[i] = S;
+  mg[n + i] += 2.0 * S / jd;
+}
 
 // Area tracking (Sec. IV, zooms of Fig. 3): is the momentum direction inside
 // [cos_lo, cos_hi] x [phi_lo, phi_hi] (phi = atan2(p_y, p_x) in [0, 2pi))?

@@ -63,7 +63,9 @@ __global__ void __launch_bounds__(256) k_iterate_df64(IterArgs a, TabDF tb, Coef
         if (TAN) {
           const float n2 = 0.5f * (t.du * t.du + t.dv * t.dv) + t.dz * t.dz +
                            0.5f * (t.dqu * t.dqu + t.dqv * t.dqv) + t.dpz * t.dpz;
-          logsum += 0.5 * (double)__logf(n2);
+          const double l = 0.5 * (double)__logf(n2);
+          logsum += l;
+          if (a.s.megno) megno_update(a.s.megno, n, i, (a.step0 + s + 1) / a.R, l);
           const float inv = rsqrtf(n2);
           t.du *= inv; t.dv *= inv; t.dz *= inv;
           t.dqu *= inv; t.dqv *= inv; t.dpz *= inv;

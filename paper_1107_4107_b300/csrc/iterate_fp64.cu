@@ -14,8 +14,9 @@
 //              dq_v += G c_v dv - 2 Sp s_v dz
 //              dp_z += A (4 tau eps g - 2 tau eps) dz - Sp (s_u du + s_v dv)
 //              (the Hessian of Eq. 2 in rotated coordinates applied to the tangent)
-// Every R steps: tangent renormalised (log of its norm accumulated) and the
-// energy error sampled; every W steps: the window velocity V (Sec. IV) closed.
+// Every R steps: tangent renormalised (log of its norm accumulated, and the
+// MEGNO sums when enabled) and the energy error sampled; every W steps: the
+// window velocity V (Sec. IV) closed.
 #include "step64.cuh"
 
 namespace arnold {
@@ -70,7 +71,9 @@ __global__ void __launch_bounds__(256) k_iterate_fp64(IterArgs a) {
         if (TAN) {
           const double n2 = 0.5 * (t.du * t.du + t.dv * t.dv) + t.dz * t.dz +
                             0.5 * (t.dqu * t.dqu + t.dqv * t.dqv) + t.dpz * t.dpz;
-          logsum += 0.5 * log(n2);
+          const double l = 0.5 * log(n2);
+          logsum += l;
+          if (a.s.megno) megno_update(a.s.megno, n, i, (a.step0 + s + 1) / a.R, l);
           const double inv = rsqrt(n2);
           t.du *= inv; t.dv *= inv; t.dz *= inv;
           t.dqu *= inv; t.dqv *= inv; t.dpz *= inv;

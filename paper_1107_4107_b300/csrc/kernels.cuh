@@ -34,6 +34,7 @@ struct ReadArgs {
   double t;             // steps * h
   double eps;
   double threshold;     // chaos threshold kappa ln(max(t, e)) / t
+  long long m;          // renormalisations so far (steps / R): the MEGNO sample index
   void* out;
 };
 

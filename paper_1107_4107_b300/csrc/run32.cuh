@@ -79,14 +79,20 @@ __device__ __forceinline__ void store32(const RunArgs32& a, long long i, const T
   a.s.demax[i] = demax;
 }
 
-// Renormalisation of the tangent (FP64 log accumulation) and FP64 energy sample.
+// Renormalisation of the tangent (FP64 log accumulation, MEGNO sums of the
+// j-th renormalisation when enabled) and FP64 energy sample.  `own` is false
+// for a padding slot that repeats another thread's trajectory: it must not
+// update the MEGNO sums a second time.
 template <bool TAN>
 __device__ __forceinline__ void renorm_sample32(const RunArgs32& a, long long i, Traj32& t, double& logsum,
-                                                double& demax, int& bad, const float2* ssc, const Tab32& tb) {
+                                                double& demax, int& bad, const float2* ssc, const Tab32& tb,
+                                                long long j, bool own) {
   if (TAN) {
     const float n2 = 0.5f * (t.du * t.du + t.dv * t.dv) + t.dz * t.dz + 0.5f * (t.dqu * t.dqu + t.dqv * t.dqv) +
                      t.dpz * t.dpz;
-    logsum += 0.5 * (double)__logf(n2);
+    const double l = 0.5 * (double)__logf(n2);
+    logsum += l;
+    if (a.s.megno && own) megno_update(a.s.megno, a.n, i, j, l);
     const float inv = rsqrtf(n2);
     t.du *= inv; t.dv *= inv; t.dz *= inv;
     t.dqu *= inv; t.dqv *= inv; t.dpz *= inv;
@@ -155,7 +161,9 @@ __device__ __forceinline__ void run_traj32(const RunArgs32& a, const Coef32& cf,
     if (--to_renorm == 0) {
       to_renorm = a.R;
 #pragma unroll
-      for (int r = 0; r < TPT; ++r) renorm_sample32<TAN>(a, idx[r], t[r], logsum[r], demax[r], bad, ssc, tb);
+      for (int r = 0; r < TPT; ++r)
+        renorm_sample32<TAN>(a, idx[r], t[r], logsum[r], demax[r], bad, ssc, tb, (step0 + s + 1) / a.R,
+                             (valid >> r) & 1);
     }
     if (a.W > 0 && --to_window == 0) {
       to_window = a.W;

@@ -57,6 +57,7 @@ __device__ __forceinline__ void init_common(const InitArgs& a, long long i, doub
   a.s.e0[i] = e0;
   a.s.demax[i] = 0.0;
   if (a.s.logsum) a.s.logsum[i] = 0.0;
+  if (a.s.megno) { a.s.megno[i] = 0.0; a.s.megno[n + i] = 0.0; }
   a.s.V[i] = 0.0; a.s.V[n + i] = 0.0; a.s.V[2 * n + i] = 0.0;
   if (a.s.left) a.s.left[i] = 0;
   if (a.tangent) {
@@ -217,6 +218,12 @@ __global__ void k_indicator(ReadArgs a) {
       }
       case ARNOLD_IND_LOGSUM:
         out[i] = a.s.logsum[i];
+        break;
+      case ARNOLD_IND_MEGNO:      // <Y>_m = Ysum / m (0 before the first renormalisation)
+        out[i] = a.m > 0 ? a.s.megno[n + i] / (double)a.m : 0.0;
+        break;
+      case ARNOLD_IND_MEGNO_Y:    // Y_m = 2 S / m
+        out[i] = a.m > 0 ? 2.0 * a.s.megno[i] / (double)a.m : 0.0;
         break;
       case ARNOLD_IND_LEFT:
         ((unsigned char*)a.out)[i] = a.s.left ? a.s.left[i] : 0;

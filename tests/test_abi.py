@@ -68,7 +68,8 @@ def test_create_rejects_bad_arguments_before_cuda(L):
     L.arnold_params_default(ctypes.byref(base))
     bad = []
     for field, val in (("h", 0.0), ("scheme", 7), ("precision", 3), ("renorm_every", 0), ("window", -1),
-                       ("chaos_kappa", 0.0), ("block_size", 48), ("tangent", 2)):
+                       ("chaos_kappa", 0.0), ("block_size", 48), ("tangent", 2), ("megno", 2),
+                       ("reserved", 1)):
         p = _lib.Params.from_buffer_copy(base)
         setattr(p, field, val)
         bad.append(p)
@@ -77,6 +78,17 @@ def test_create_rejects_bad_arguments_before_cuda(L):
         assert rc == _lib.EINVAL and not h.value
     rc, _ = _create(L, base, n=0)
     assert rc == _lib.EINVAL
+    # MEGNO is a tangent indicator: megno = 1 with the tangent off is rejected
+    p = _lib.Params.from_buffer_copy(base)
+    p.megno, p.tangent = 1, 0
+    rc, h = _create(L, p)
+    assert rc == _lib.EINVAL and not h.value
+
+
+def test_params_struct_matches_the_header():
+    """The ctypes mirror has the C layout: 8 + 8 + 4 * 4 + 8 + 8 + 4 * 4 bytes."""
+    assert ctypes.sizeof(_lib.Params) == 64
+    assert _lib.Params.megno.offset == 56 and _lib.Params.reserved.offset == 60
 
 
 def test_alloc_fault_injection_on_host():
