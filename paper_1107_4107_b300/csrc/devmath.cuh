@@ -1,5 +1,6 @@
 // Device math shared by the kernels of libarnold: angle wrapping and sincos.
 #pragma once
+#include <cstring>
 #include "arnold_internal.cuh"
 
 namespace arnold {
@@ -22,29 +23,146 @@ __device__ __forceinline__ void wrap_angle(double& u, int& lap) {
   }
 }
 
+// Bit views of FP64 / FP32 values, usable on the host as well (the sincos
+// below is checked against long-double libm by a host harness).
+__host__ __device__ __forceinline__ unsigned long long f64_bits(double x) {
+#ifdef __CUDA_ARCH__
+  return (unsigned long long)__double_as_longlong(x);
+#else
+  unsigned long long b;
+  memcpy(&b, &x, 8);
+  return b;
+#endif
+}
+__host__ __device__ __forceinline__ double f64_from_bits(unsigned long long b) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)b);
+#else
+  double x;
+  memcpy(&x, &b, 8);
+  return x;
+#endif
+}
+__host__ __device__ __forceinline__ unsigned int f32_bits(float x) {
+#ifdef __CUDA_ARCH__
+  return __float_as_uint(x);
+#else
+  unsigned int b;
+  memcpy(&b, &x, 4);
+  return b;
+#endif
+}
+__host__ __device__ __forceinline__ float f32_from_bits(unsigned int b) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(b);
+#else
+  float x;
+  memcpy(&x, &b, 4);
+  return x;
+#endif
+}
+
+// x = hi + lo + e with hi the leading 24 significand bits of x and lo the
+// next 23 (both truncated toward zero), |e| < 2^-46 |x|, from the IEEE bits
+// with integer and FP32 operations only (an FP64 -> FP32 conversion costs an
+// FP64 issue slot on this part).  lo = 0 for |x| < 2^-80, hi = 0 for
+// |x| < 2^-126.
+__host__ __device__ __forceinline__ void split_f64(double x, float& hi, float& lo) {
+  const unsigned long long b = f64_bits(x);
+  const unsigned int h = (unsigned int)(b >> 32), l = (unsigned int)b;
+  const int e = (int)((h >> 20) & 0x7FFu);
+  const unsigned int sign = h & 0x80000000u;
+  const unsigned int mh = ((h & 0xFFFFFu) << 3) | (l >> 29);
+  hi = e > 896 ? f32_from_bits(sign | ((unsigned int)(e - 896) << 23) | mh) : 0.0f;
+  // the next 23 significand bits as an exact FP32 integer, scaled by 2^(e - 1069)
+  const float m = f32_from_bits(0x4B000000u | ((l & 0x1FFFFFFFu) >> 6)) - 8388608.0f;
+  const float scale = f32_from_bits((unsigned int)(e > 942 ? e - 942 : 1) << 23);
+  lo = e > 942 ? f32_from_bits(f32_bits(m * scale) ^ sign) : 0.0f;
+}
+
+// The FP64 value of a normalised float pair (|b| <= ulp(a) / 2), assembled in
+// 64-bit integer arithmetic: a's significand at bits 52..29, b's aligned
+// below it and added or subtracted, one normalising shift.  Bits of b below
+// a's 53-bit window are dropped (error < 1 ulp of the result).
+__host__ __device__ __forceinline__ double pair_to_f64(float a, float b) {
+  const unsigned int ua = f32_bits(a), ub = f32_bits(b);
+  const int ea = (int)((ua >> 23) & 0xFFu), eb = (int)((ub >> 23) & 0xFFu);
+  if (ea == 0) return 0.0;
+  const unsigned long long A = (unsigned long long)((ua & 0x7FFFFFu) | 0x800000u) << 29;
+  const int k = ea - eb;
+  unsigned long long B = 0;
+  if (eb != 0 && k >= 24 && k < 53) {
+    const unsigned long long mb = (ub & 0x7FFFFFu) | 0x800000u;
+    B = k <= 29 ? mb << (29 - k) : mb >> (k - 29);
+  }
+  unsigned long long M = ((ua ^ ub) & 0x80000000u) ? A - B : A + B;
+  int E = ea + 896;   // FP64 biased exponent of a's binade
+  if (M >> 53) { M >>= 1; ++E; }
+  else if (!(M >> 52)) { M <<= 1; --E; }
+  return f64_from_bits(((unsigned long long)(ua & 0x80000000u) << 32) | ((unsigned long long)E << 52) |
+                       (M & 0xFFFFFFFFFFFFFULL));
+}
+
+// Knuth's TwoSum on FP32 (host and device; the build keeps FP32 operations
+// uncontracted).
+__host__ __device__ __forceinline__ void tsum32(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
 // FP64 sincos for x in [0, 2pi] by table lookup (Tang, "Table-lookup
 // algorithms for elementary functions", 1991): x = theta_j + r with
-// |r| <= D/2 ~ 7.7e-4, sin x = S cos r + C sin r, cos x = C cos r - S sin r,
-// with Taylor polynomials sin r = r - r^3/6 (next term < 3e-18) and
-// cos r - 1 = -r^2/2 + r^4/24 (next term < 3e-22).  10 FP64 instructions.
-// The index j is taken from a truncated FP32 copy of x built with integer
-// operations, so it costs no FP64 slot; j is clamped to the table.
-__device__ __forceinline__ void sincos_tab64(double x, const double2* __restrict__ sc,
-                                             const double* __restrict__ th, double& s, double& c) {
-  constexpr float kInvD = (float)(kTabN / kTwoPi);
-  int hi = __double2hiint(x);
-  hi = max(hi, 0x38000000);                            // x < 2^-126 (or negative) -> index 0
-  float xf = __int_as_float((hi - 0x38000000) << 3);   // FP32 exponent/mantissa from the FP64 bits
-  float t = fmaf(xf, kInvD, 12582912.0f);              // 1.5 * 2^23: round-to-nearest integer in the low bits
-  int j = __float_as_int(t) - 0x4B400000;
-  j = min(max(j, 0), kTabN);
+// |r| <= D/2 ~ 7.7e-4, theta_j = j D exact, so r = x - theta_j is exact, and
+//   sin x = S + ds,  ds = C (r + sm) + S cm,
+//   cos x = C + dc,  dc = C cm - S (r + sm),
+// with sm = sin r - r = -r^3/6 + r^5/120 (next term < 3e-22) and
+// cm = cos r - 1 = -r^2/2 + r^4/24 (next term < 3e-22).  Only r and the two
+// final additions run in FP64 (3 FP64 instructions; the FP64 pipe is 1/74 of
+// the FP32 one here).  The corrections |ds|, |dc| <= 7.7e-4 are formed in
+// double-float arithmetic on the FP32 pipes from integer splits of r, S and C
+// (relative error ~2^-46, i.e. < 1e-17 absolute) and joined back to FP64 in
+// integer arithmetic, so the result keeps FP64 accuracy (the final rounding
+// dominates: <= ~1.3e-16).  The index j comes from a truncated FP32 copy of
+// x built with integer operations; j is clamped to the table.
+__host__ __device__ __forceinline__ void sincos_tab64(double x, const double2* __restrict__ sc,
+                                                      const double* __restrict__ th, double& s, double& c) {
+  const float kInvD = (float)(kTabN / kTwoPi);
+  int hi = (int)(f64_bits(x) >> 32);
+  hi = hi > 0x38000000 ? hi : 0x38000000;               // x < 2^-126 (or negative) -> index 0
+  const float xf = f32_from_bits((unsigned int)(hi - 0x38000000) << 3);   // FP32 bits from the FP64 bits
+  const float t = fmaf(xf, kInvD, 12582912.0f);         // 1.5 * 2^23: round-to-nearest integer in the low bits
+  int j = (int)f32_bits(t) - 0x4B400000;
+  j = j < 0 ? 0 : (j > kTabN ? kTabN : j);
   const double2 e = sc[j];
   const double r = x - th[j];
-  const double r2 = r * r;
-  const double sr = fma(r2 * r, -1.0 / 6.0, r);
-  const double cm = r2 * fma(r2, 1.0 / 24.0, -0.5);
-  s = fma(e.y, sr, fma(e.x, cm, e.x));
-  c = fma(-e.x, sr, fma(e.y, cm, e.y));
+  float rh, rl, Sh, Sl, Ch, Cl;
+  split_f64(r, rh, rl);
+  split_f64(e.x, Sh, Sl);
+  split_f64(e.y, Ch, Cl);
+  const float r2h = rh * rh;
+  const float r2l = fmaf(rh + rh, rl, fmaf(rh, rh, -r2h));
+  const float cmh = -0.5f * r2h;                                        // exact
+  const float cml = fmaf(r2h * r2h, 1.0f / 24.0f, -0.5f * r2l);
+  const float sm = (r2h * rh) * fmaf(r2h, 1.0f / 120.0f, -1.0f / 6.0f);
+  // C r and S r as pairs (TwoProd), S cm and C cm as pairs
+  const float cr = Ch * rh, cre = fmaf(Cl, rh, fmaf(Ch, rl, fmaf(Ch, rh, -cr)));
+  const float sr = Sh * rh, sre = fmaf(Sl, rh, fmaf(Sh, rl, fmaf(Sh, rh, -sr)));
+  const float scm = Sh * cmh, scme = fmaf(Sl, cmh, fmaf(Sh, cml, fmaf(Sh, cmh, -scm)));
+  const float ccm = Ch * cmh, ccme = fmaf(Cl, cmh, fmaf(Ch, cml, fmaf(Ch, cmh, -ccm)));
+  float a, ae, dh, dl;
+  tsum32(cr, scm, a, ae);
+  tsum32(a, ((ae + cre) + scme) + Ch * sm, dh, dl);
+  s = e.x + pair_to_f64(dh, dl);
+  tsum32(ccm, -sr, a, ae);
+  tsum32(a, ((ae + ccme) - sre) - Sh * sm, dh, dl);
+  c = e.y + pair_to_f64(dh, dl);
+  // |r| < 2^-60 (the split would flush it): sin x = S + r [j = 0], cos x = C,
+  // exact in FP64; selected with an integer test, no FP64 instruction.
+  if (((f64_bits(r) >> 52) & 0x7FFu) < 963u) {
+    s = j == 0 ? r : e.x;
+    c = e.y;
+  }
 }
 
 // Copy the FP64 sincos tables into shared memory (whole block participates).
