@@ -38,11 +38,12 @@ G, E, EPS = 2048, 400.0, 1.0
 H = 0.02 * math.pi
 HORIZON = 1_000_000
 # FP64 instructions and FLOPs (FMA = 2) per composite step, counted from the
-# kernel source (iterate_fp64.cu, devmath.cuh) for Yoshida-6A with tangent:
-# kick = 3 sincos (10 instr / 16 flop each) + force (8 / 11) + tangent (14 / 22),
+# kernel source (iterate_fp64.cu, step64.cuh, devmath.cuh) for Yoshida-6A with
+# tangent: kick = 3 sincos (3 instr / 3 flop each: r and the two final sums;
+# the corrections run on the FP32 pipes) + force (8 / 11) + tangent (14 / 22),
 # drift = 6 FMA (6 / 12); 7 kicks + 8 drifts.
-FP64_INSTR_PER_STEP = 7 * (3 * 10 + 8 + 14) + 8 * 6
-FP64_FLOP_PER_STEP = 7 * (3 * 16 + 11 + 22) + 8 * 12
+FP64_INSTR_PER_STEP = 7 * (3 * 3 + 8 + 14) + 8 * 6
+FP64_FLOP_PER_STEP = 7 * (3 * 3 + 11 + 22) + 8 * 12
 # FP32C: FP32/INT arithmetic per composite step counted from the source
 # (step32.cuh): kick = 3 sincos (12 each) + force with TwoSum adds (5 + 3 +
 # 3 * 7) + tangent (14); drift = 3 * (4 product + 6 TwoSum + 2) + 3 tangent;
@@ -51,6 +52,9 @@ FP32C_INSTR_PER_STEP = 7 * (3 * 12 + 29 + 14) + 8 * (3 * 12 + 3) + 6 * 3 + 6
 # Measured by ncu for k_iterate_fp32c<7,true,false> (all pipes, per map step):
 # profiles/k_iterate_fp32c__grid2048_E400_1M_traj_400_steps.md
 FP32C_ISSUED_PER_STEP_NCU = 1024
+# Measured by ncu for k_iterate_fp64<7,true> (all pipes: FP64, FP32, INT, LSU):
+# profiles/k_iterate_fp64__grid2048_E400_1M_traj_20_steps.md
+FP64_ISSUED_PER_STEP_NCU = None
 
 
 def parse():
@@ -258,12 +262,18 @@ def main():
     map_steps_per_launch = n * args.chunk / launches_per_iterate
     achieved_flops = map_steps_per_launch * FP64_FLOP_PER_STEP / (per_launch_ms * 1e-3)
     pipe_instr = map_steps_per_launch * FP64_INSTR_PER_STEP / (per_launch_ms * 1e-3)
+    # The binding unit is the FP64 pipe: achieved = FP64 instructions per second
+    # of the dominant kernel (source count x map steps / CUDA-event launch time),
+    # peak = the live DFMA probe (one FP64 instruction per lane-slot).
     roofline = {"bound": "alu", "kernel": "k_iterate_fp64<7,true>",
-                "achieved": achieved_flops / 1e12, "peak": 2 * dfma / 1e12, "unit": "TFLOP/s",
-                "frac": achieved_flops / (2 * dfma), "traffic": traffic_for("k_iterate_fp64"),
-                "peak_source": "measured live: DFMA probe (arnold_probe_peak), FMA = 2 FLOP",
-                "fp64_pipe_frac": pipe_instr / dfma,
-                "flop_per_map_step": FP64_FLOP_PER_STEP, "fp64_instr_per_map_step": FP64_INSTR_PER_STEP}
+                "achieved": pipe_instr / 1e12, "peak": dfma / 1e12, "unit": "T FP64-instr/s",
+                "frac": pipe_instr / dfma, "traffic": traffic_for("k_iterate_fp64"),
+                "peak_source": "measured live: DFMA probe (arnold_probe_peak)",
+                "fp64_instr_per_map_step": FP64_INSTR_PER_STEP,
+                "fp64_tflops": achieved_flops / 1e12, "flop_per_map_step": FP64_FLOP_PER_STEP,
+                "issued_instr_per_map_step_ncu": FP64_ISSUED_PER_STEP_NCU,
+                "issue_frac": (map_steps_per_launch / (per_launch_ms * 1e-3) * FP64_ISSUED_PER_STEP_NCU / ffma
+                               if FP64_ISSUED_PER_STEP_NCU else None)}
 
     # ---- end to end through the C ABI with host buffers (pinned) ----
     e2e = None

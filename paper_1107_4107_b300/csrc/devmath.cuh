@@ -87,20 +87,20 @@ __host__ __device__ __forceinline__ void split_f64(double x, float& hi, float& l
 __host__ __device__ __forceinline__ double pair_to_f64(float a, float b) {
   const unsigned int ua = f32_bits(a), ub = f32_bits(b);
   const int ea = (int)((ua >> 23) & 0xFFu), eb = (int)((ub >> 23) & 0xFFu);
-  if (ea == 0) return 0.0;
   const unsigned long long A = (unsigned long long)((ua & 0x7FFFFFu) | 0x800000u) << 29;
   const int k = ea - eb;
-  unsigned long long B = 0;
-  if (eb != 0 && k >= 24 && k < 53) {
-    const unsigned long long mb = (ub & 0x7FFFFFu) | 0x800000u;
-    B = k <= 29 ? mb << (29 - k) : mb >> (k - 29);
-  }
-  unsigned long long M = ((ua ^ ub) & 0x80000000u) ? A - B : A + B;
-  int E = ea + 896;   // FP64 biased exponent of a's binade
-  if (M >> 53) { M >>= 1; ++E; }
-  else if (!(M >> 52)) { M <<= 1; --E; }
-  return f64_from_bits(((unsigned long long)(ua & 0x80000000u) << 32) | ((unsigned long long)E << 52) |
-                       (M & 0xFFFFFFFFFFFFFULL));
+  const unsigned long long mb = (ub & 0x7FFFFFu) | 0x800000u;
+  // b's significand in units of a's 53-bit window (selects, no branches)
+  const int kl = (k >= 0 && k <= 29) ? 29 - k : 0, kr = k <= 29 ? 0 : (k < 53 ? k - 29 : 63);
+  unsigned long long B = (mb << kl) >> kr;
+  B = (eb != 0 && k >= 24) ? B : 0ULL;
+  const unsigned long long M0 = ((ua ^ ub) & 0x80000000u) ? A - B : A + B;
+  const bool up = (M0 >> 53) != 0, down = (M0 >> 52) == 0;
+  const unsigned long long M = up ? M0 >> 1 : (down ? M0 << 1 : M0);
+  const unsigned long long E = (unsigned long long)(ea + 896 + (up ? 1 : 0) - (down ? 1 : 0));
+  const double d = f64_from_bits(((unsigned long long)(ua & 0x80000000u) << 32) | (E << 52) |
+                                 (M & 0xFFFFFFFFFFFFFULL));
+  return ea != 0 ? d : 0.0;
 }
 
 // Knuth's TwoSum on FP32 (host and device; the build keeps FP32 operations
@@ -159,10 +159,9 @@ __host__ __device__ __forceinline__ void sincos_tab64(double x, const double2* _
   c = e.y + pair_to_f64(dh, dl);
   // |r| < 2^-60 (the split would flush it): sin x = S + r [j = 0], cos x = C,
   // exact in FP64; selected with an integer test, no FP64 instruction.
-  if (((f64_bits(r) >> 52) & 0x7FFu) < 963u) {
-    s = j == 0 ? r : e.x;
-    c = e.y;
-  }
+  const bool tiny = ((f64_bits(r) >> 52) & 0x7FFu) < 963u;
+  s = tiny ? (j == 0 ? r : e.x) : s;
+  c = tiny ? e.y : c;
 }
 
 // Copy the FP64 sincos tables into shared memory (whole block participates).

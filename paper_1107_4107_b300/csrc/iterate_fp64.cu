@@ -28,7 +28,14 @@ __global__ void __launch_bounds__(256) k_iterate_fp64(IterArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   double2* ssc = reinterpret_cast<double2*>(smem);
   double* sth = reinterpret_cast<double*>(smem + kTabEntries * sizeof(double2));
-  load_tab64(a.sc, a.th, ssc, sth);
+  // step coefficients in shared memory: the substep loop below is not unrolled
+  __shared__ double s_sig[10], s_k2[9], s_k4[9];
+  if (threadIdx.x < 10) s_sig[threadIdx.x] = a.cf.sig[threadIdx.x];
+  if (threadIdx.x < 9) {
+    s_k2[threadIdx.x] = a.cf.k2[threadIdx.x];
+    s_k4[threadIdx.x] = a.cf.k4[threadIdx.x];
+  }
+  load_tab64(a.sc, a.th, ssc, sth);   // ends with a block barrier
 
   const long long n = a.n;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -60,11 +67,13 @@ __global__ void __launch_bounds__(256) k_iterate_fp64(IterArgs a) {
 
 #pragma unroll 1
     for (int s = 0; s < a.nsteps; ++s) {
-      drift64<TAN>(t, a.cf.sig[0]);
-#pragma unroll
+      drift64<TAN>(t, s_sig[0]);
+      // Not unrolled: seven inlined kicks with their double-float sincos
+      // overflow the instruction cache (ncu: fetch stalls).
+#pragma unroll 1
       for (int k = 0; k < M; ++k) {
-        kick64<TAN>(t, a.cf.k2[k], a.cf.k4[k], ssc, sth);
-        drift64<TAN>(t, a.cf.sig[k + 1]);
+        kick64<TAN>(t, s_k2[k], s_k4[k], ssc, sth);
+        drift64<TAN>(t, s_sig[k + 1]);
       }
       if (--to_renorm == 0) {
         to_renorm = a.R;
