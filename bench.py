@@ -39,11 +39,11 @@ H = 0.02 * math.pi
 HORIZON = 1_000_000
 # FP64 instructions and FLOPs (FMA = 2) per composite step, counted from the
 # kernel source (iterate_fp64.cu, step64.cuh, devmath.cuh) for Yoshida-6A with
-# tangent: kick = 3 sincos (3 instr / 3 flop each: r and the two final sums;
-# the corrections run on the FP32 pipes) + force (8 / 11) + tangent (14 / 22),
-# drift = 6 FMA (6 / 12); 7 kicks + 8 drifts.
-FP64_INSTR_PER_STEP = 7 * (3 * 3 + 8 + 14) + 8 * 6
-FP64_FLOP_PER_STEP = 7 * (3 * 3 + 11 + 22) + 8 * 12
+# tangent: kick = 3 sincos (2 instr / 2 flop each: the two final sums; the
+# reduction and the corrections run on the integer and FP32 pipes) + force
+# (7 / 10) + tangent (13 / 20); drift = 6 FMA (6 / 12); 7 kicks + 8 drifts.
+FP64_INSTR_PER_STEP = 7 * (3 * 2 + 7 + 13) + 8 * 6
+FP64_FLOP_PER_STEP = 7 * (3 * 2 + 10 + 20) + 8 * 12
 # FP32C: FP32/INT arithmetic per composite step counted from the source
 # (step32.cuh): kick = 3 sincos (12 each) + force with TwoSum adds (5 + 3 +
 # 3 * 7) + tangent (14); drift = 3 * (4 product + 6 TwoSum + 2) + 3 tangent;

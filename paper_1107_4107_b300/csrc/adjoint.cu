@@ -35,7 +35,8 @@ __device__ __forceinline__ void adj_kick64(double& lu, double& lv, double& lz, d
   sincos_tab64(t.v, sc, th, sv, cv);
   sincos_tab64(t.z, sc, th, sz, cz);
   const double g = cz * cz, sh = sz * cz;
-  const double G = k2 * g, Sp = k2 * sh, A = cu + cv;
+  const double kc = k2 * cz;
+  const double G = kc * cz, Sp = kc * sz, A = cu + cv;   // as the forward kick forms them
   const double F = fma(lqu * su, g, fma(lqv * sv, g, lpz * (sh * A)));
   gh = fma(ch, F, gh);
   ge = fma(ce, F, ge);
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(256) k_adjoint_fp64(AdjArgs a) {
       drift64<false>(t, a.cf.sig[0]);
 #pragma unroll
       for (int k = 0; k < M; ++k) {
-        kick64<false>(t, a.cf.k2[k], a.cf.k4[k], ssc, sth);
+        kick64<false>(t, a.cf.k2[k], ssc, sth);
         drift64<false>(t, a.cf.sig[k + 1]);
       }
       double* sg = a.seg64 + (long long)s * 6 * n;

@@ -103,6 +103,54 @@ __host__ __device__ __forceinline__ double pair_to_f64(float a, float b) {
   return ea != 0 ? d : 0.0;
 }
 
+__host__ __device__ __forceinline__ int clz64(unsigned long long v) {
+#ifdef __CUDA_ARCH__
+  return __clzll((long long)v);
+#else
+  return v ? __builtin_clzll(v) : 64;
+#endif
+}
+
+// r = x - t as a float pair (rh, rl), for t >= 0 and t = 0 or x / t in
+// [1/4, 4] (then r is exact in FP64, Sterbenz): the significands are aligned
+// and subtracted in 64-bit integers and the difference cut into its leading
+// 24 and next 23 bits (truncated; |error| < 2^-46 |r|), with no FP64
+// instruction.  |r| < 2^-126 gives rh = 0, |r| < 2^-80 gives rl = 0.
+__host__ __device__ __forceinline__ void reduce_pair(double x, double t, float& rh, float& rl) {
+  const unsigned long long bx = f64_bits(x), bt = f64_bits(t);
+  const int ex = (int)((bx >> 52) & 0x7FFu), et = (int)(bt >> 52);
+  const long long mx0 = (long long)((bx & 0xFFFFFFFFFFFFFULL) | (ex ? 0x10000000000000ULL : 0ULL));
+  const long long mx = (bx >> 63) ? -mx0 : mx0;
+  const long long mt = (long long)((bt & 0xFFFFFFFFFFFFFULL) | (et ? 0x10000000000000ULL : 0ULL));
+  const int ex1 = ex ? ex : 1, et1 = et ? et : 1;    // subnormals share the exponent of 2^-1022
+  const int e0 = (mt == 0 || ex1 < et1) ? ex1 : et1;
+  const int sx = ex1 - e0, st = et1 - e0;          // 0..2 when both are non-zero
+  const long long R = (mx << (sx < 8 ? sx : 8)) - (mt == 0 ? 0LL : (mt << (st < 8 ? st : 8)));
+  const unsigned int sign = R < 0 ? 0x80000000u : 0u;
+  const unsigned long long U = (unsigned long long)(R < 0 ? -R : R);
+  const int lz = clz64(U);
+  const unsigned long long top = U << (lz & 63);
+  const int p = 63 - lz + e0;                       // r = 1.xxx * 2^(p - 1075)
+  const int fh = p - 948, fl = p - 994;             // FP32 exponent fields of rh and of rl's unit
+  rh = (U != 0 && fh >= 1) ? f32_from_bits(sign | ((unsigned int)fh << 23) | ((unsigned int)(top >> 40) & 0x7FFFFFu))
+                           : 0.0f;
+  const float m = f32_from_bits(0x4B000000u | ((unsigned int)(top >> 17) & 0x7FFFFFu)) - 8388608.0f;
+  const float sc = f32_from_bits((unsigned int)(fl >= 1 ? fl : 1) << 23);
+  rl = (U != 0 && fl >= 1) ? f32_from_bits(f32_bits(m * sc) ^ sign) : 0.0f;
+}
+
+// 2x and -2x exactly, by an exponent increment (and a sign flip) on the
+// IEEE bits: integer operations instead of an FP64 multiply.  Zero and
+// subnormal x (|x| < 2^-1022) give x and -x.
+__host__ __device__ __forceinline__ double times2(double x) {
+  const unsigned long long b = f64_bits(x);
+  return ((b >> 52) & 0x7FFu) ? f64_from_bits(b + (1ULL << 52)) : x;
+}
+__host__ __device__ __forceinline__ double neg_times2(double x) {
+  const unsigned long long b = f64_bits(x) ^ 0x8000000000000000ULL;
+  return ((b >> 52) & 0x7FFu) ? f64_from_bits(b + (1ULL << 52)) : f64_from_bits(b);
+}
+
 // Knuth's TwoSum on FP32 (host and device; the build keeps FP32 operations
 // uncontracted).
 __host__ __device__ __forceinline__ void tsum32(float a, float b, float& s, float& e) {
@@ -113,13 +161,14 @@ __host__ __device__ __forceinline__ void tsum32(float a, float b, float& s, floa
 
 // FP64 sincos for x in [0, 2pi] by table lookup (Tang, "Table-lookup
 // algorithms for elementary functions", 1991): x = theta_j + r with
-// |r| <= D/2 ~ 7.7e-4, theta_j = j D exact, so r = x - theta_j is exact, and
+// |r| <= D/2 ~ 7.7e-4, theta_j = j D exact, so r = x - theta_j is exact
+// (formed as a float pair in integer arithmetic), and
 //   sin x = S + ds,  ds = C (r + sm) + S cm,
 //   cos x = C + dc,  dc = C cm - S (r + sm),
 // with sm = sin r - r = -r^3/6 + r^5/120 (next term < 3e-22) and
-// cm = cos r - 1 = -r^2/2 + r^4/24 (next term < 3e-22).  Only r and the two
-// final additions run in FP64 (3 FP64 instructions; the FP64 pipe is 1/74 of
-// the FP32 one here).  The corrections |ds|, |dc| <= 7.7e-4 are formed in
+// cm = cos r - 1 = -r^2/2 + r^4/24 (next term < 3e-22).  Only the two final
+// additions run in FP64 (2 FP64 instructions; the FP64 pipe is 1/74 of the
+// FP32 one here).  The corrections |ds|, |dc| <= 7.7e-4 are formed in
 // double-float arithmetic on the FP32 pipes from integer splits of r, S and C
 // (relative error ~2^-46, i.e. < 1e-17 absolute) and joined back to FP64 in
 // integer arithmetic, so the result keeps FP64 accuracy (the final rounding
@@ -135,9 +184,8 @@ __host__ __device__ __forceinline__ void sincos_tab64(double x, const double2* _
   int j = (int)f32_bits(t) - 0x4B400000;
   j = j < 0 ? 0 : (j > kTabN ? kTabN : j);
   const double2 e = sc[j];
-  const double r = x - th[j];
   float rh, rl, Sh, Sl, Ch, Cl;
-  split_f64(r, rh, rl);
+  reduce_pair(x, th[j], rh, rl);                         // r = x - theta_j, exact, no FP64 slot
   split_f64(e.x, Sh, Sl);
   split_f64(e.y, Ch, Cl);
   const float r2h = rh * rh;
@@ -157,11 +205,11 @@ __host__ __device__ __forceinline__ void sincos_tab64(double x, const double2* _
   tsum32(ccm, -sr, a, ae);
   tsum32(a, ((ae + ccme) - sre) - Sh * sm, dh, dl);
   c = e.y + pair_to_f64(dh, dl);
-  // |r| < 2^-60 (the split would flush it): sin x = S + r [j = 0], cos x = C,
-  // exact in FP64; selected with an integer test, no FP64 instruction.
-  const bool tiny = ((f64_bits(r) >> 52) & 0x7FFu) < 963u;
-  s = tiny ? (j == 0 ? r : e.x) : s;
-  c = tiny ? e.y : c;
+  // x < 2^-60 (the pair would flush r = x): sin x = x, cos x = 1, exact in
+  // FP64; selected with an integer test, no FP64 instruction.
+  const bool tiny = (f64_bits(x) >> 52) < 963u;
+  s = tiny ? x : s;
+  c = tiny ? 1.0 : c;
 }
 
 // Copy the FP64 sincos tables into shared memory (whole block participates).

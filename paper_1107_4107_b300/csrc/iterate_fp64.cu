@@ -29,12 +29,9 @@ __global__ void __launch_bounds__(256) k_iterate_fp64(IterArgs a) {
   double2* ssc = reinterpret_cast<double2*>(smem);
   double* sth = reinterpret_cast<double*>(smem + kTabEntries * sizeof(double2));
   // step coefficients in shared memory: the substep loop below is not unrolled
-  __shared__ double s_sig[10], s_k2[9], s_k4[9];
+  __shared__ double s_sig[10], s_k2[9];
   if (threadIdx.x < 10) s_sig[threadIdx.x] = a.cf.sig[threadIdx.x];
-  if (threadIdx.x < 9) {
-    s_k2[threadIdx.x] = a.cf.k2[threadIdx.x];
-    s_k4[threadIdx.x] = a.cf.k4[threadIdx.x];
-  }
+  if (threadIdx.x < 9) s_k2[threadIdx.x] = a.cf.k2[threadIdx.x];
   load_tab64(a.sc, a.th, ssc, sth);   // ends with a block barrier
 
   const long long n = a.n;
@@ -72,7 +69,7 @@ __global__ void __launch_bounds__(256) k_iterate_fp64(IterArgs a) {
       // overflow the instruction cache (ncu: fetch stalls).
 #pragma unroll 1
       for (int k = 0; k < M; ++k) {
-        kick64<TAN>(t, s_k2[k], s_k4[k], ssc, sth);
+        kick64<TAN>(t, s_k2[k], ssc, sth);
         drift64<TAN>(t, s_sig[k + 1]);
       }
       if (--to_renorm == 0) {
