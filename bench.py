@@ -54,7 +54,7 @@ FP32C_INSTR_PER_STEP = 7 * (3 * 12 + 29 + 14) + 8 * (3 * 12 + 3) + 6 * 3 + 6
 FP32C_ISSUED_PER_STEP_NCU = 1024
 # Measured by ncu for k_iterate_fp64<7,true> (all pipes: FP64, FP32, INT, LSU):
 # profiles/k_iterate_fp64__grid2048_E400_1M_traj_20_steps.md
-FP64_ISSUED_PER_STEP_NCU = None
+FP64_ISSUED_PER_STEP_NCU = 8018
 
 
 def parse():
