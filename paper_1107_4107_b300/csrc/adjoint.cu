@@ -49,17 +49,24 @@ __device__ __forceinline__ void adj_kick64(double& lu, double& lv, double& lz, d
   t.pz = fma(-Sp, A, t.pz);
 }
 
+// Step coefficients of the FP64 adjoint, staged in shared memory (the
+// substep loops are not unrolled: the inlined kicks would overflow the
+// instruction cache).
+struct AdjCoef64 {
+  double sig[10], k2[9], k4[9], ch[9], ce[9], cd[10];
+};
+
 // Reverse sweep of one step: from the step's end state, undo drift m, kick
 // m-1, ..., drift 0 (positions and momenta within the step are regained by
 // running the step backwards; they match the forward ones to rounding),
 // applying the adjoint of each operation on the way.
 template <int M>
 __device__ __forceinline__ void reverse_step64(Traj64& t, double& lu, double& lv, double& lz, double& lqu,
-                                               double& lqv, double& lpz, double& gh, double& ge, const AdjArgs& a,
+                                               double& lqv, double& lpz, double& gh, double& ge, const AdjCoef64& a,
                                                const double2* sc, const double* th) {
-#pragma unroll
+#pragma unroll 1
   for (int k = M; k >= 0; --k) {
-    const double sg = a.cf.sig[k];
+    const double sg = a.sig[k];
     gh = fma(a.cd[k], fma(lu, t.qu, fma(lv, t.qv, lz * t.pz)), gh);
     lqu = fma(sg, lu, lqu);
     lqv = fma(sg, lv, lqv);
@@ -70,7 +77,7 @@ __device__ __forceinline__ void reverse_step64(Traj64& t, double& lu, double& lv
     wrap_angle(t.u, t.lu);
     wrap_angle(t.v, t.lv);
     wrap_angle(t.z, t.lz);
-    if (k > 0) adj_kick64(lu, lv, lz, lqu, lqv, lpz, t, a.cf.k2[k - 1], a.cf.k4[k - 1], a.ch[k - 1], a.ce[k - 1], gh, ge, sc, th);
+    if (k > 0) adj_kick64(lu, lv, lz, lqu, lqv, lpz, t, a.k2[k - 1], a.k4[k - 1], a.ch[k - 1], a.ce[k - 1], gh, ge, sc, th);
   }
 }
 
@@ -79,7 +86,18 @@ __global__ void __launch_bounds__(256) k_adjoint_fp64(AdjArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   double2* ssc = reinterpret_cast<double2*>(smem);
   double* sth = reinterpret_cast<double*>(smem + kTabEntries * sizeof(double2));
-  load_tab64(a.sc, a.th, ssc, sth);
+  __shared__ AdjCoef64 cf;
+  if (threadIdx.x < 10) {
+    cf.sig[threadIdx.x] = a.cf.sig[threadIdx.x];
+    cf.cd[threadIdx.x] = a.cd[threadIdx.x];
+  }
+  if (threadIdx.x < 9) {
+    cf.k2[threadIdx.x] = a.cf.k2[threadIdx.x];
+    cf.k4[threadIdx.x] = a.cf.k4[threadIdx.x];
+    cf.ch[threadIdx.x] = a.ch[threadIdx.x];
+    cf.ce[threadIdx.x] = a.ce[threadIdx.x];
+  }
+  load_tab64(a.sc, a.th, ssc, sth);   // ends with a block barrier
   const long long n = a.n;
   const double* ck = a.ck64 + (long long)a.k * 6 * n;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -90,11 +108,11 @@ __global__ void __launch_bounds__(256) k_adjoint_fp64(AdjArgs a) {
     // pass 1: the state after every step of the segment (slot s = end of step s)
 #pragma unroll 1
     for (int s = 0; s < a.steps; ++s) {
-      drift64<false>(t, a.cf.sig[0]);
-#pragma unroll
+      drift64<false>(t, cf.sig[0]);
+#pragma unroll 1
       for (int k = 0; k < M; ++k) {
-        kick64<false>(t, a.cf.k2[k], ssc, sth);
-        drift64<false>(t, a.cf.sig[k + 1]);
+        kick64<false>(t, cf.k2[k], ssc, sth);
+        drift64<false>(t, cf.sig[k + 1]);
       }
       double* sg = a.seg64 + (long long)s * 6 * n;
       sg[i] = t.u; sg[n + i] = t.v; sg[2 * n + i] = t.z;
@@ -109,7 +127,7 @@ __global__ void __launch_bounds__(256) k_adjoint_fp64(AdjArgs a) {
       const double* sg = a.seg64 + (long long)s * 6 * n;
       t.u = sg[i]; t.v = sg[n + i]; t.z = sg[2 * n + i];
       t.qu = sg[3 * n + i]; t.qv = sg[4 * n + i]; t.pz = sg[5 * n + i];
-      reverse_step64<M>(t, lu, lv, lz, lqu, lqv, lpz, gh, ge, a, ssc, sth);
+      reverse_step64<M>(t, lu, lv, lz, lqu, lqv, lpz, gh, ge, cf, ssc, sth);
     }
     a.lam[i] = lu; a.lam[n + i] = lv; a.lam[2 * n + i] = lz;
     a.lam[3 * n + i] = lqu; a.lam[4 * n + i] = lqv; a.lam[5 * n + i] = lpz;
