@@ -165,7 +165,8 @@ __host__ __device__ __forceinline__ void tsum32(float a, float b, float& s, floa
 // (formed as a float pair in integer arithmetic), and
 //   sin x = S + ds,  ds = C (r + sm) + S cm,
 //   cos x = C + dc,  dc = C cm - S (r + sm),
-// with sm = sin r - r = -r^3/6 + r^5/120 (next term < 3e-22) and
+// with sm = sin r - r = -r^3/6 + r^5/120 (next term < 3e-22; r^3/6 as a
+// float pair) and
 // cm = cos r - 1 = -r^2/2 + r^4/24 (next term < 3e-22).  Only the two final
 // additions run in FP64 (2 FP64 instructions; the FP64 pipe is 1/74 of the
 // FP32 one here).  The corrections |ds|, |dc| <= 7.7e-4 are formed in
@@ -192,18 +193,31 @@ __host__ __device__ __forceinline__ void sincos_tab64(double x, const double2* _
   const float r2l = fmaf(rh + rh, rl, fmaf(rh, rh, -r2h));
   const float cmh = -0.5f * r2h;                                        // exact
   const float cml = fmaf(r2h * r2h, 1.0f / 24.0f, -0.5f * r2l);
-  const float sm = (r2h * rh) * fmaf(r2h, 1.0f / 120.0f, -1.0f / 6.0f);
-  // C r and S r as pairs (TwoProd), S cm and C cm as pairs
-  const float cr = Ch * rh, cre = fmaf(Cl, rh, fmaf(Ch, rl, fmaf(Ch, rh, -cr)));
+  // sin r - r = -r^3/6 + r^5/120 with r^3/6 as a pair (1/6 = k6h + k6l)
+  constexpr float k6h = 0.16666667163372039794921875f;       // 1/6 rounded to FP32
+  constexpr float k6l = -4.96705373128255208333e-09f;         // 1/6 - k6h
+  const float r3 = r2h * rh;
+  const float r3e = fmaf(r2h, rl, fmaf(r2l, rh, fmaf(r2h, rh, -r3)));
+  const float q = r3 * k6h;
+  const float qe = fmaf(r3, k6l, fmaf(r3e, k6h, fmaf(r3, k6h, -q)));
+  const float smh = -q;
+  const float sml = fmaf(r3 * r2h, 1.0f / 120.0f, -qe);
+  // C r and S r as pairs (TwoProd), S cm and C cm as pairs.  For j = 0 the
+  // C r = r term is left to the FP64 sum (sin x = x + (sin r - r)), which
+  // keeps sin x relatively accurate near 0.
+  const bool j0 = j == 0;
+  const float rhc = j0 ? 0.0f : rh, rlc = j0 ? 0.0f : rl;
+  const float cr = Ch * rhc, cre = fmaf(Cl, rhc, fmaf(Ch, rlc, fmaf(Ch, rhc, -cr)));
   const float sr = Sh * rh, sre = fmaf(Sl, rh, fmaf(Sh, rl, fmaf(Sh, rh, -sr)));
   const float scm = Sh * cmh, scme = fmaf(Sl, cmh, fmaf(Sh, cml, fmaf(Sh, cmh, -scm)));
   const float ccm = Ch * cmh, ccme = fmaf(Cl, cmh, fmaf(Ch, cml, fmaf(Ch, cmh, -ccm)));
-  float a, ae, dh, dl;
+  float a, ae, b, be, dh, dl;
   tsum32(cr, scm, a, ae);
-  tsum32(a, ((ae + cre) + scme) + Ch * sm, dh, dl);
-  s = e.x + pair_to_f64(dh, dl);
+  tsum32(a, Ch * smh, b, be);
+  tsum32(b, (((ae + be) + cre) + scme) + Ch * sml, dh, dl);
+  s = (j0 ? x : e.x) + pair_to_f64(dh, dl);
   tsum32(ccm, -sr, a, ae);
-  tsum32(a, ((ae + ccme) - sre) - Sh * sm, dh, dl);
+  tsum32(a, ((ae + ccme) - sre) - Sh * (smh + sml), dh, dl);
   c = e.y + pair_to_f64(dh, dl);
   // x < 2^-60 (the pair would flush r = x): sin x = x, cos x = 1, exact in
   // FP64; selected with an integer test, no FP64 instruction.

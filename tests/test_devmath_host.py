@@ -5,7 +5,9 @@ this CPU test builds them with nvcc for the host and checks them against exact
 references and long-double libm: the join is exact for normalised pairs, the
 split loses < 2^-46 relative, the integer reduction equals the FP64 one, and
 sin/cos stay within 1.5e-16 absolute (the device test holds the GPU build to
-5e-16)."""
+5e-16), with sin x relatively accurate near 0 (elsewhere the bound is
+absolute: ~1e-17 from the double-float corrections plus the final FP64
+rounding)."""
 import json
 import os
 import shutil
@@ -30,4 +32,5 @@ def test_devmath_building_blocks_on_host(tmp_path):
     assert r["split_f64_rel"] <= 2.0 ** -46, r
     assert r["reduce_pair_mismatch"] == 0, r
     assert r["sin_abs"] < 1.5e-16 and r["cos_abs"] < 1.5e-16, r
-    assert r["tiny_sin_rel"] == 0.0, r
+    # table index 0 (x < D/2): sin x = x + (sin x - x) keeps ~1 ulp relative accuracy
+    assert r["tiny_sin_rel"] < 5e-16, r

@@ -93,7 +93,7 @@ def test_fp32c_vs_fp64_gpu_scan_agreement(E):
     assert agree >= 0.995 and l1 <= 1e-2
 
 
-def test_fp32c_reduce64_variant_matches():
+def test_fp32c_reduce64_variant_matches(tmp_path):
     """The FP64 mod-2pi reduction variant (ARNOLD_FP32C_REDUCE64=1) agrees with the
     float-pair reduction to FP32C accuracy; run in a child process because the
     switch is read at context creation."""
@@ -101,16 +101,14 @@ def test_fp32c_reduce64_variant_matches():
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    import tempfile
     outs = []
-    with tempfile.TemporaryDirectory() as tmp:
-        for flag in ("0", "1"):
-            path = os.path.join(tmp, f"r{flag}.npy")
-            code = ("import numpy as np; from paper_1107_4107_b300 import inputs; "
-                    "from paper_1107_4107_b300.api import ArnoldEnsemble as A; X,P=inputs.box(256, seed=3); "
-                    "e=A(256, precision='fp32c'); e.set_state(X,P); e.iterate(100); "
-                    f"np.save({path!r}, np.concatenate([e.indicator('dX'), e.indicator('P')]))")
-            env = dict(os.environ, ARNOLD_FP32C_REDUCE64=flag, PYTHONPATH=root)
-            subprocess.check_call([sys.executable, "-c", code], env=env, cwd=root)
-            outs.append(np.load(path))
+    for flag in ("0", "1"):
+        path = str(tmp_path / f"r{flag}.npy")
+        code = ("import numpy as np; from paper_1107_4107_b300 import inputs; "
+                "from paper_1107_4107_b300.api import ArnoldEnsemble as A; X,P=inputs.box(256, seed=3); "
+                "e=A(256, precision='fp32c'); e.set_state(X,P); e.iterate(100); "
+                f"np.save({path!r}, np.concatenate([e.indicator('dX'), e.indicator('P')]))")
+        env = dict(os.environ, ARNOLD_FP32C_REDUCE64=flag, PYTHONPATH=root)
+        subprocess.check_call([sys.executable, "-c", code], env=env, cwd=root)
+        outs.append(np.load(path))
     assert rel_err(outs[0], outs[1]) < 1e-6
