@@ -175,7 +175,12 @@ __global__ void k_indicator(ReadArgs a) {
       u = a.s.st[i]; v = a.s.st[n + i]; z = a.s.st[2 * n + i];
       qu = a.s.st[3 * n + i]; qv = a.s.st[4 * n + i]; pz = a.s.st[5 * n + i];
     }
-    const int lu = a.s.lap[i], lv = a.s.lap[n + i], lz = a.s.lap[2 * n + i];
+    int lu = a.s.lap[i], lv = a.s.lap[n + i], lz = a.s.lap[2 * n + i];
+    if (a.fp32c) {   // pair states keep angles unreduced between exact reductions: bring them into [0, 2pi)
+      lu += reduce_any(u);
+      lv += reduce_any(v);
+      lz += reduce_any(z);
+    }
     double* out = (double*)a.out;
     switch (a.kind) {
       case ARNOLD_IND_X: {

@@ -112,3 +112,24 @@ def test_fp32c_reduce64_variant_matches(tmp_path):
         subprocess.check_call([sys.executable, "-c", code], env=env, cwd=root)
         outs.append(np.load(path))
     assert rel_err(outs[0], outs[1]) < 1e-6
+
+
+@pytest.mark.parametrize("precision", ["fp32c", "df64"])
+def test_pair_state_readout_angles_and_energy_error(precision):
+    """Pair states hold angles unreduced between exact reductions (FP32C up to 64 rad):
+    the read-out must still give X in [0, 2pi) and dE = |H(X, P) - H(X0, P0)| evaluated
+    in FP64 from the exported state (identity check of the read-out arithmetic,
+    independent of the propagation error)."""
+    X0, P0 = inputs.box(300, seed=31)
+    ens = _ens(300, precision=precision)
+    ens.set_state(X0, P0)
+    ens.iterate(150)           # box momenta ~ (10, 4, 25): angles pass 64 rad before the first reduction
+    X = ens.indicator("X")
+    P = ens.indicator("P")
+    assert np.all(X >= 0.0) and np.all(X < 2 * np.pi)
+    e0 = oracle.energy(1.0, X0, P0)
+    dE_ref = np.abs(oracle.energy(1.0, X, P) - e0)
+    assert np.max(np.abs(ens.indicator("dE") - dE_ref)) < 1e-11
+    # the unwrapped displacement is unaffected by the read-out reduction
+    st = oracle.State(X0, P0, oracle_params()).advance(150)
+    assert rel_err(ens.indicator("dX"), st.unwrapped_displacement()) < 3e-6
