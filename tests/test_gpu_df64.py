@@ -117,3 +117,16 @@ def test_df64_resume_bitwise_and_no_adjoint():
     with pytest.raises(ArnoldError) as ex:
         b.forward_ckpt(10)
     assert ex.value.status == EUNSUPPORTED
+
+
+def test_df64_full_size_grid_sampled_cells():
+    """The 2048 x 2048 scan in double-float (default launch configuration): 256 sampled
+    cells against the FP64 oracle one by one, 100 steps."""
+    G, E = 2048, 400.0
+    e = _ens(G * G)
+    e.init_grid(G, E)
+    e.iterate(100)
+    cells = inputs.sample_cells(G * G, 256, seed=5)
+    st = oracle_grid_state(G, E, oracle_params(), cells=cells).advance(100, threads=4)
+    assert rel_err(e.indicator("dX")[:, cells], st.unwrapped_displacement()) < TOL
+    assert rel_err(e.indicator("P")[:, cells], st.P) < TOL

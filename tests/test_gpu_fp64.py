@@ -258,3 +258,35 @@ def test_stats_of_ensemble_consistent_with_indicators(torch_cuda):
     assert s["n"] == 4096 and s["under"] + s["over"] + s["hist"].sum() == 4096
     assert s["dE_max"] == ens.indicator("dE_max").max()
     np.testing.assert_allclose(s["p_var"], np.var(ens.indicator("P"), axis=1), rtol=1e-12)
+
+
+def _hist_l1(a, b):
+    """L1 distance of the normalised histograms of log10 chi (200 bins on [-8, 1])."""
+    ha, _ = np.histogram(np.log10(np.clip(a, 1e-300, None)), bins=200, range=(-8, 1))
+    hb, _ = np.histogram(np.log10(np.clip(b, 1e-300, None)), bins=200, range=(-8, 1))
+    return float(np.abs(ha / len(a) - hb / len(b)).sum())
+
+
+@pytest.mark.parametrize("E", [400.0, 40.0])
+def test_oracle_scale_scan_128x128_1e4_steps(torch_cuda, E):
+    """The whole oracle-scale scan (128 x 128 grid, 16,384 trajectories, 1e4 steps with
+    tangent) against the oracle run of the same configuration.  Past the Lyapunov time
+    chaotic trajectories decorrelate, so the bar is the scan-level one: class agreement
+    >= 99.5 %, chi-histogram L1 <= 1e-2; low-growth cells (chi t < 5) also agree on the
+    log sum of the tangent to 1e-6."""
+    import os
+    G = 128
+    ens = _ens(G * G)
+    ens.init_grid(G, E)
+    ens.iterate(10000)
+    st = oracle_grid_state(G, E, oracle_params()).advance(10000, threads=max(1, os.cpu_count() or 1))
+    cls, chi = ens.indicator("class"), ens.indicator("chi")
+    agree = float(np.mean(cls == st.classify()))
+    l1 = _hist_l1(chi, st.chi())
+    low = st.chi() * st.time() < 5.0
+    dlog = float(np.max(np.abs(chi[low] - st.chi()[low]))) * st.time()
+    print(f"E={E}: agreement {agree:.5f}, L1 {l1:.2e}, chaotic {cls.mean():.4f}, "
+          f"low-growth cells {low.mean():.3f} with max |d log sum| {dlog:.2e}")
+    assert agree >= 0.995
+    assert l1 <= 1e-2
+    assert dlog < 1e-6
