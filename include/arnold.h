@@ -162,6 +162,18 @@ int arnold_set_state_shell(arnold_ctx* ctx, const double* x, const double* p, in
  * Flags reset at set_state / init_grid / this call.  Errors: EINVAL, ENOMEM. */
 int arnold_track_patch(arnold_ctx* ctx, double cos_lo, double cos_hi, double phi_lo, double phi_hi);
 
+/* Snapshots of V (Sec. IV: one F per window Delta t): while enabled, the kernel
+ * that closes averaging window w (w = 1, 2, ... counted from the last clock
+ * reset; window = W steps, W > 0 in the params) also writes that window's V
+ * into slot w - 1 of v_snap, a caller-owned DEVICE array [k_max][3][n] f64
+ * (x, y, z components, SoA), for w <= k_max; later windows are not stored.
+ * One long arnold_iterate thus records every window without host round
+ * trips.  v_snap must stay valid until the iterations that write it have
+ * completed on the stream; NULL disables.  The library keeps only the pointer
+ * (not part of checkpoints).  Errors: EINVAL (window = 0, k_max < 1, pointer
+ * not 8-byte aligned). */
+int arnold_set_snapshots(arnold_ctx* ctx, double* v_snap, int64_t k_max);
+
 /* Density of V on the momentum sphere (F of Sec. IV, Figs. 2-4): counts of the
  * direction of V (ARNOLD_IND_V) in n_cos x n_phi equal-width cells of
  * cos theta in [cos_lo, cos_hi] and phi in [phi_lo, phi_hi]; directions

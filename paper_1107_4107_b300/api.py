@@ -140,6 +140,21 @@ class ArnoldEnsemble:
                                                    ko, int(accumulate)), "arnold_velocity_histogram")
         return out
 
+    def set_snapshots(self, v_snap=None):
+        """Record V of window w into v_snap[w - 1] (a torch CUDA float64 tensor
+        [k][3][n], kept alive by the caller) as the kernels close windows; None
+        disables."""
+        if v_snap is None:
+            check(_lib.lib().arnold_set_snapshots(self._h, None, 0), "arnold_set_snapshots")
+            self._snap = None
+            return
+        if not _is_torch(v_snap) or not v_snap.is_cuda or v_snap.dtype != __import__("torch").float64 \
+                or v_snap.dim() != 3 or tuple(v_snap.shape[1:]) != (3, self.n) or not v_snap.is_contiguous():
+            raise ValueError(f"v_snap must be a contiguous CUDA float64 tensor [k][3][{self.n}]")
+        check(_lib.lib().arnold_set_snapshots(self._h, ctypes.c_void_p(v_snap.data_ptr()), int(v_snap.shape[0])),
+              "arnold_set_snapshots")
+        self._snap = v_snap
+
     def iterate(self, n_steps: int):
         check(_lib.lib().arnold_iterate(self._h, int(n_steps)), "arnold_iterate")
 

@@ -619,6 +619,19 @@ int arnold_iterate(arnold_ctx* c, int64_t n_steps) {
 
 int64_t arnold_steps_done(const arnold_ctx* c) { return c ? c->steps : -1; }
 
+int arnold_set_snapshots(arnold_ctx* c, double* v_snap, int64_t k_max) {
+  if (!c) return ARNOLD_EINVAL;
+  if (!v_snap) {
+    c->s.snap = nullptr;
+    c->s.snap_k = 0;
+    return ARNOLD_OK;
+  }
+  if (c->prm.window <= 0 || k_max < 1 || ((uintptr_t)v_snap & 7)) return ARNOLD_EINVAL;
+  c->s.snap = v_snap;
+  c->s.snap_k = k_max;
+  return ARNOLD_OK;
+}
+
 int64_t arnold_launch_count(const arnold_ctx* c) { return c ? c->launches : -1; }
 
 int arnold_indicator(arnold_ctx* c, int kind, void* out, int ptr_kind) {

@@ -59,7 +59,21 @@ struct Fp64State {
   unsigned char* left;  // [n] area tracking: 1 once the momentum direction left the patch (null = off)
   double patch[4];      // cos_lo, cos_hi, phi_lo, phi_hi of the tracked patch
   double* megno;        // [2][n] MEGNO sums S = sum_j j l_j and Ysum = sum_j Y_j (null = off)
+  double* snap;         // [snap_k][3][n] V of window w in slot w - 1 (caller-owned device memory; null = off)
+  long long snap_k;     // slots in snap
 };
+
+// Snapshot of the V of window w (w = 1, 2, ... from the clock reset) into slot
+// w - 1 of the caller's [snap_k][3][n] array, if there is one and it has room.
+__device__ __forceinline__ void snapshot_v(const Fp64State& s, long long n, long long i, long long w, double vx,
+                                           double vy, double vz) {
+  if (s.snap && w >= 1 && w <= s.snap_k) {
+    double* o = s.snap + (w - 1) * 3 * n;
+    o[i] = vx;
+    o[n + i] = vy;
+    o[2 * n + i] = vz;
+  }
+}
 
 // MEGNO (Cincotta & Simo 2000) sampled at the renormalisation points: at the
 // j-th renormalisation (j counted from the start of the run) with log growth

@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(256) k_iterate_df64(IterArgs a, TabDF tb, Coef
       }
       if (a.W > 0 && --to_window == 0) {
         to_window = a.W;
-        close_window32(ra, i, t);
+        close_window32(ra, i, t, (a.step0 + s + 1) / a.W);
       }
     }
     store32<TAN>(ra, i, t, logsum, demax);

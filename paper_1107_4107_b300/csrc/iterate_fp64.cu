@@ -96,9 +96,11 @@ __global__ void __launch_bounds__(256) k_iterate_fp64(IterArgs a) {
         const double dU = (t.u - a.s.ref[i]) + kTwoPi * (double)(t.lu - a.s.lapref[i]);
         const double dV = (t.v - a.s.ref[n + i]) + kTwoPi * (double)(t.lv - a.s.lapref[n + i]);
         const double dZ = (t.z - a.s.ref[2 * n + i]) + kTwoPi * (double)(t.lz - a.s.lapref[2 * n + i]);
-        a.s.V[i] = 0.5 * (dU + dV) * inv_dt;
-        a.s.V[n + i] = 0.5 * (dU - dV) * inv_dt;
-        a.s.V[2 * n + i] = dZ * inv_dt;
+        const double vx = 0.5 * (dU + dV) * inv_dt, vy = 0.5 * (dU - dV) * inv_dt, vz = dZ * inv_dt;
+        a.s.V[i] = vx;
+        a.s.V[n + i] = vy;
+        a.s.V[2 * n + i] = vz;
+        snapshot_v(a.s, n, i, (a.step0 + s + 1) / a.W, vx, vy, vz);
         a.s.ref[i] = t.u; a.s.ref[n + i] = t.v; a.s.ref[2 * n + i] = t.z;
         a.s.lapref[i] = t.lu; a.s.lapref[n + i] = t.lv; a.s.lapref[2 * n + i] = t.lz;
       }

@@ -113,8 +113,9 @@ __device__ __forceinline__ void renorm_sample32(const RunArgs32& a, long long i,
   }
 }
 
-// Close an averaging window of V (Sec. IV) for trajectory i.
-__device__ __forceinline__ void close_window32(const RunArgs32& a, long long i, const Traj32& t) {
+// Close averaging window w (counted from the clock reset) of V (Sec. IV) for
+// trajectory i.
+__device__ __forceinline__ void close_window32(const RunArgs32& a, long long i, const Traj32& t, long long w) {
   const long long n = a.n;
   const double inv_dt = 1.0 / ((double)a.W * a.h);
   const double u = (double)t.u.hi + (double)t.u.lo, v = (double)t.v.hi + (double)t.v.lo,
@@ -122,9 +123,11 @@ __device__ __forceinline__ void close_window32(const RunArgs32& a, long long i, 
   const double dU = (u - a.s.ref[i]) + kTwoPi * (double)(t.lu - a.s.lapref[i]);
   const double dV = (v - a.s.ref[n + i]) + kTwoPi * (double)(t.lv - a.s.lapref[n + i]);
   const double dZ = (z - a.s.ref[2 * n + i]) + kTwoPi * (double)(t.lz - a.s.lapref[2 * n + i]);
-  a.s.V[i] = 0.5 * (dU + dV) * inv_dt;
-  a.s.V[n + i] = 0.5 * (dU - dV) * inv_dt;
-  a.s.V[2 * n + i] = dZ * inv_dt;
+  const double vx = 0.5 * (dU + dV) * inv_dt, vy = 0.5 * (dU - dV) * inv_dt, vz = dZ * inv_dt;
+  a.s.V[i] = vx;
+  a.s.V[n + i] = vy;
+  a.s.V[2 * n + i] = vz;
+  snapshot_v(a.s, n, i, w, vx, vy, vz);
   a.s.ref[i] = u;
   a.s.ref[n + i] = v;
   a.s.ref[2 * n + i] = z;
@@ -169,7 +172,7 @@ __device__ __forceinline__ void run_traj32(const RunArgs32& a, const Coef32& cf,
       to_window = a.W;
 #pragma unroll
       for (int r = 0; r < TPT; ++r)
-        if (valid & (1 << r)) close_window32(a, idx[r], t[r]);
+        if (valid & (1 << r)) close_window32(a, idx[r], t[r], (step0 + s + 1) / a.W);
     }
   }
 #pragma unroll

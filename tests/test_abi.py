@@ -103,6 +103,7 @@ def test_alloc_fault_injection_on_host():
 
 def test_null_handles_are_rejected(L):
     assert L.arnold_iterate(None, 1) == _lib.EINVAL
+    assert L.arnold_set_snapshots(None, None, 0) == _lib.EINVAL
     assert L.arnold_sync(None) == _lib.EINVAL
     assert L.arnold_steps_done(None) == -1
     L.arnold_destroy(None)
