@@ -1,5 +1,9 @@
 // FP64 ensemble propagator: one thread per trajectory, state and tangent in
-// registers for a whole launch, FP64 sincos tables in shared memory.
+// registers for a whole launch, FP64 sincos tables in shared memory.  The
+// FP64 pipe (1/74 of the FP32 one on this part) is the binding unit, so FP64
+// instructions are spent only where FP64 accuracy needs them: 230 per
+// composite step (sincos corrections, reductions, wraps and exponent scalings
+// run on the integer and FP32 pipes; see devmath.cuh and step64.cuh).
 //
 // Per composite step (paper Sec. III: sixth-order symplectic integrator,
 // read as a symmetric composition of drift-kick-drift leapfrogs with
