@@ -17,7 +17,6 @@ namespace {
 struct CoefDF {
   float sh[10], sl[10];   // drifts as float pairs
   Pair k2[9];             // 2 tau eps as pairs
-  float k4f[9];
 };
 
 // The substep loop is not unrolled: a double-float kick is ~350 instructions,
@@ -54,7 +53,7 @@ __global__ void __launch_bounds__(256) k_iterate_df64(IterArgs a, TabDF tb, Coef
       drift32<TAN>(t, cf.sh[0], cf.sl[0]);
 #pragma unroll 1
       for (int k = 0; k < M; ++k) {
-        kick_df<TAN>(t, cf.k2[k], cf.k4f[k], stab, tb);
+        kick_df<TAN>(t, cf.k2[k], stab, tb);
         drift32<TAN>(t, cf.sh[k + 1], cf.sl[k + 1]);
       }
       end_step_df(t, tb);
@@ -75,7 +74,9 @@ __global__ void __launch_bounds__(256) k_iterate_df64(IterArgs a, TabDF tb, Coef
         const double dE = fabs(kin + a.eps * potential_df(t, stab, tb) - a.s.e0[i]);
         demax = fmax(demax, dE);
         if (!isfinite(dE)) bad = 1;
-        // the table's exact index range needs |angle| < 25 inside a step
+        // angles start a step below 12 rad and move at most h |q| within it (the
+        // drift weights' partial sums stay in [0, 1]): below 21 < 25 rad, the
+        // table's exact index range, while h |q| <= 9
         const float qmax = fmaxf(fmaxf(fabsf(t.qu.hi), fabsf(t.qv.hi)), fabsf(t.pz.hi));
         if (qmax * fabsf(hf) > 9.0f) atomicOr(a.flags, kFlagRange);
         if (a.s.left) {
@@ -115,7 +116,6 @@ CoefDF coef_df(const StepCoef& c) {
   for (int k = 0; k < 9; ++k) {
     r.k2[k].hi = (float)c.k2[k];
     r.k2[k].lo = (float)(c.k2[k] - (double)r.k2[k].hi);
-    r.k4f[k] = c.k4f[k];
   }
   return r;
 }

@@ -31,6 +31,17 @@ __device__ __forceinline__ Pair df_mul(const Pair& a, const Pair& b) {
   return r;
 }
 
+// Product without the final renormalisation: (p, e) with |e| up to ~2 ulp(p),
+// for products that feed another product or an accumulation.
+__device__ __forceinline__ Pair df_mul_u(const Pair& a, const Pair& b) {
+  Pair r;
+  r.hi = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -r.hi);
+  e = fmaf(a.hi, b.lo, e);
+  r.lo = fmaf(a.lo, b.hi, e);
+  return r;
+}
+
 __device__ __forceinline__ Pair df_sqr(const Pair& a) {
   const float p = __fmul_rn(a.hi, a.hi);
   float e = fmaf(a.hi, a.hi, -p);
@@ -116,27 +127,27 @@ __device__ __forceinline__ void sincos_df(const Pair& x, const float4* __restric
 }
 
 // Kick in double-float: q_u += G s_u, q_v += G s_v, p_z += Sp A with
-// G = k2 c_z^2, Sp = k2 s_z c_z, A = c_u + c_v (k2 = 2 tau eps as a pair);
-// the tangent update uses the leading words in FP32 (as in the FP32C path).
+// G = (k2 c_z) c_z, Sp = (k2 c_z) s_z, A = c_u + c_v (k2 = 2 tau eps as a
+// pair); the tangent update uses the leading words in FP32 (as in the FP32C
+// path), its 4 tau eps c_z^2 as 2G.
 template <bool TAN>
-__device__ __forceinline__ void kick_df(Traj32& t, const Pair& k2, float k4f, const float4* tab, const TabDF& tb) {
+__device__ __forceinline__ void kick_df(Traj32& t, const Pair& k2, const float4* tab, const TabDF& tb) {
   Pair su, cu, sv, cv, sz, cz;
   sincos_df(t.u, tab, tb, su, cu);
   sincos_df(t.v, tab, tb, sv, cv);
   sincos_df(t.z, tab, tb, sz, cz);
-  const Pair g = df_sqr(cz);
-  const Pair sh = df_mul(sz, cz);
-  const Pair G = df_mul(k2, g);
-  const Pair Sp = df_mul(k2, sh);
+  const Pair kc = df_mul_u(k2, cz);
+  const Pair G = df_mul_u(kc, cz);    // k2 c_z^2
+  const Pair Sp = df_mul_u(kc, sz);   // k2 s_z c_z
   const Pair A = df_add(cu, cv);
-  df_acc(t.qu, df_mul(G, su));
-  df_acc(t.qv, df_mul(G, sv));
-  df_acc(t.pz, df_mul(Sp, A));
+  df_acc(t.qu, df_mul_u(G, su));
+  df_acc(t.qv, df_mul_u(G, sv));
+  df_acc(t.pz, df_mul_u(Sp, A));
   if (TAN) {
-    const float Gf = G.hi, Spf = Sp.hi, Af = A.hi, gf = g.hi, k2f = k2.hi;
+    const float Gf = G.hi, Spf = Sp.hi, Af = A.hi, k2f = k2.hi;
     const float Gu = Gf * cu.hi, Gv = Gf * cv.hi;
     const float Yu = Spf * su.hi, Yv = Spf * sv.hi;
-    const float Z = Af * fmaf(k4f, gf, -k2f);
+    const float Z = Af * fmaf(2.0f, Gf, -k2f);   // A (k4 c_z^2 - k2), k4 = 2 k2
     const float m2dz = -2.0f * t.dz;
     t.dqu = fmaf(Gu, t.du, t.dqu);
     t.dqu = fmaf(Yu, m2dz, t.dqu);
@@ -163,9 +174,11 @@ __device__ __forceinline__ double potential_df(const Traj32& t, const float4* ta
 
 namespace arnold {
 
-// End of a DF64 step: renormalise every pair and remove whole turns from the
-// angles (exactly, 2 pi as three floats), every step, so that each kick's
-// argument stays within the table's exact index range.
+// End of a DF64 step: renormalise every pair, and once an angle passes 12 rad
+// remove whole turns from the angles (exactly, 2 pi as three floats).  With at
+// most 9 rad per step (checked at renormalisation, ERANGE otherwise) every
+// kick's argument stays below 21 rad, inside the table's exact index range
+// (|x| < 25).
 __device__ __forceinline__ void reduce_angle_df(Pair& x, int& lap, const TabDF& tb) {
   const float t = fmaf(x.hi, tb.inv2pi, 12582912.0f);
   const float kf = __fsub_rn(t, 12582912.0f);
@@ -181,9 +194,13 @@ __device__ __forceinline__ void reduce_angle_df(Pair& x, int& lap, const TabDF& 
 __device__ __forceinline__ void end_step_df(Traj32& t, const TabDF& tb) {
   renorm(t.qu); renorm(t.qv); renorm(t.pz);
   renorm(t.u); renorm(t.v); renorm(t.z);
-  reduce_angle_df(t.u, t.lu, tb);
-  reduce_angle_df(t.v, t.lv, tb);
-  reduce_angle_df(t.z, t.lz, tb);
+  const int big = max(max(__float_as_int(t.u.hi) & 0x7FFFFFFF, __float_as_int(t.v.hi) & 0x7FFFFFFF),
+                      __float_as_int(t.z.hi) & 0x7FFFFFFF);
+  if (big > 0x41400000) {   // |angle| > 12
+    reduce_angle_df(t.u, t.lu, tb);
+    reduce_angle_df(t.v, t.lv, tb);
+    reduce_angle_df(t.z, t.lz, tb);
+  }
 }
 
 }  // namespace arnold
