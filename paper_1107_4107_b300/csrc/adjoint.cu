@@ -148,7 +148,8 @@ __device__ __forceinline__ void adj_kick32(float& lu, float& lv, float& lz, floa
   sincos_tab32(t.v, sc, tb, sv, cv);
   sincos_tab32(t.z, sc, tb, sz, cz);
   const float g = cz * cz, sh = sz * cz;
-  const float G = k2 * g, Sp = k2 * sh, A = cu + cv;
+  const float kc = k2 * cz;
+  const float G = kc * cz, Sp = kc * sz, A = cu + cv;   // as the forward kick forms them
   const float F = fmaf(lqu * su, g, fmaf(lqv * sv, g, lpz * (sh * A)));
   acc_pair(gh, ch * F);
   acc_pair(ge, ce * F);
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(256) k_adjoint_fp32c(AdjArgs a, Tab32 tb) {
       drift32<false>(t, a.cf.sig_hi[0], a.cf.sig_lo[0]);
 #pragma unroll
       for (int k = 0; k < M; ++k) {
-        kick32<false>(t, a.cf.k2f[k], a.cf.k4f[k], ssc, tb);
+        kick32<false>(t, a.cf.k2f[k], ssc, tb);
         drift32<false>(t, a.cf.sig_hi[k + 1], a.cf.sig_lo[k + 1]);
       }
       end_step32<false>(t, tb);

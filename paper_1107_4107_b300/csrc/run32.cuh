@@ -155,7 +155,7 @@ __device__ __forceinline__ void run_traj32(const RunArgs32& a, const Coef32& cf,
 #pragma unroll
     for (int k = 0; k < M; ++k) {
 #pragma unroll
-      for (int r = 0; r < TPT; ++r) kick32<TAN>(t[r], cf.k2[k], cf.k4[k], ssc, tb);
+      for (int r = 0; r < TPT; ++r) kick32<TAN>(t[r], cf.k2[k], ssc, tb);
 #pragma unroll
       for (int r = 0; r < TPT; ++r) drift32<TAN>(t[r], cf.sh[k + 1], cf.sl[k + 1]);
     }

@@ -137,15 +137,14 @@ __device__ __forceinline__ void drift32(Traj32& t, float sh, float sl) {
 }
 
 template <bool TAN>
-__device__ __forceinline__ void kick32(Traj32& t, float k2, float k4, const float2* sc, const Tab32& tb) {
+__device__ __forceinline__ void kick32(Traj32& t, float k2, const float2* sc, const Tab32& tb) {
   float su, cu, sv, cv, sz, cz;
   sincos_tab32(t.u, sc, tb, su, cu);
   sincos_tab32(t.v, sc, tb, sv, cv);
   sincos_tab32(t.z, sc, tb, sz, cz);
-  const float g = cz * cz;
-  const float sh = sz * cz;
-  const float G = k2 * g;
-  const float Sp = k2 * sh;
+  const float kc = k2 * cz;
+  const float G = kc * cz;    // k2 c_z^2
+  const float Sp = kc * sz;   // k2 s_z c_z
   const float A = cu + cv;
   add_comp(t.qu, G * su);
   add_comp(t.qv, G * sv);
@@ -153,7 +152,7 @@ __device__ __forceinline__ void kick32(Traj32& t, float k2, float k4, const floa
   if (TAN) {
     const float Gu = G * cu, Gv = G * cv;
     const float Yu = Sp * su, Yv = Sp * sv;
-    const float Z = A * fmaf(k4, g, -k2);
+    const float Z = A * fmaf(2.0f, G, -k2);   // A (k4 c_z^2 - k2), k4 = 2 k2
     const float m2dz = -2.0f * t.dz;
     t.dqu = fmaf(Gu, t.du, t.dqu);
     t.dqu = fmaf(Yu, m2dz, t.dqu);
