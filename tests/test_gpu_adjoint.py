@@ -143,3 +143,52 @@ def test_autograd_function_variance_loss():
     assert _rel(Pt.grad.cpu().numpy(), op) < 1e-9
     assert abs(h.grad.item() - oh) <= 1e-9 * abs(oh)
     assert abs(eps.grad.item() - oe) <= 1e-9 * abs(oe)
+
+
+def test_sharded_variance_gradient_equals_whole_ensemble():
+    """Two shards of one ensemble, each with its own context and CUDA adjoint, run
+    the sharded variance-loss gradient (loss partials exchanged before the reverse
+    sweep, (h, eps) partials after it) in two host threads with an in-process
+    exchange; the result equals the gradient of the whole ensemble."""
+    import threading
+
+    from paper_1107_4107_b300 import shard
+    from paper_1107_4107_b300.api import ArnoldEnsemble
+    n, N, cut = 4096, 200, 1500
+    X, P = inputs.box(n, seed=23)
+    whole = ArnoldEnsemble(n, tangent=False)
+    whole.set_state(X, P)
+    whole.forward_ckpt(N)
+    PN = whole.indicator("P")
+    up = (2.0 / 3.0) * (PN - PN.mean(axis=1, keepdims=True)) / n
+    gx, gp, gh, ge = whole.grad(dL_dp=up)
+
+    slots, barrier, results = [None, None], threading.Barrier(2), [None, None]
+
+    def exchange_for(r):
+        def ex(obj):
+            slots[r] = obj
+            barrier.wait()
+            out = list(slots)
+            barrier.wait()
+            return out
+        return ex
+
+    def run(r, lo, hi):
+        e = ArnoldEnsemble(hi - lo, tangent=False)
+        e.set_state(X[:, lo:hi].copy(), P[:, lo:hi].copy())
+        e.forward_ckpt(N)
+        results[r] = shard.variance_loss_grad(e.indicator("P"), lambda u: e.grad(dL_dp=u), exchange_for(r))
+        e.close()
+
+    th = [threading.Thread(target=run, args=(0, 0, cut)), threading.Thread(target=run, args=(1, cut, n))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    for r, (lo, hi) in enumerate(((0, cut), (cut, n))):
+        L, sgx, sgp, sgh, sge = results[r]
+        assert abs(L - float(np.mean(np.var(PN, axis=1)))) <= 1e-13 * L
+        np.testing.assert_allclose(sgx, gx[:, lo:hi], rtol=1e-12, atol=1e-16)
+        np.testing.assert_allclose(sgp, gp[:, lo:hi], rtol=1e-12, atol=1e-16)
+        np.testing.assert_allclose([sgh, sge], [float(gh), float(ge)], rtol=1e-12)

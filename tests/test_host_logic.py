@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_1107_4107_b300 import params, shard
+from paper_1107_4107_b300 import inputs, params, shard
 
 
 def test_parameter_conversions():
@@ -116,3 +116,68 @@ def test_two_rank_gloo_merge(tmp_path):
     assert list(got[nb:nb + 4]) == [whole["under"], whole["over"], whole["chaotic"], n]
     np.testing.assert_allclose(got[nb + 4:nb + 7], whole["p_mean"], rtol=1e-12)
     np.testing.assert_allclose(got[nb + 7:nb + 10], whole["p_var"], rtol=1e-12)
+
+
+def _adjoint_case():
+    X, P = inputs.box(24, seed=17)
+    prm = oracle.Params(renorm_every=100)
+    return prm, X, P, 40
+
+
+def _adjoint_rank_main(rank, world, port, out_path):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    prm, X, P, N = _adjoint_case()
+    r0, cnt = shard.row_band(X.shape[1], rank, world)
+    Xl, Pl = X[:, r0:r0 + cnt], P[:, r0:r0 + cnt]
+    PN = oracle.State(Xl, Pl, prm, tangent=False).advance(N).P
+
+    def local_backward(up):
+        gx, gp, gh, ge, _, _ = oracle.gradient(prm, Xl, Pl, N, dL_dpN=up)
+        return gx, gp, gh, ge
+
+    L, gx, gp, gh, ge = shard.variance_loss_grad(PN, local_backward, shard.dist_exchange())
+    np.save(out_path + f".{rank}.npy", np.concatenate([[L, gh, ge], gx.ravel(), gp.ravel()]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_gloo_sharded_adjoint(tmp_path):
+    """World size 2 over gloo on CPU: the sharded variance-loss gradient (loss
+    partials exchanged before the reverse sweep, (h, eps) partials after it), with
+    the oracle's forward-mode gradient as each rank's local backward, equals the
+    oracle gradient of the whole ensemble."""
+    import socket
+
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    out = str(tmp_path / "adj")
+    mp.start_processes(_adjoint_rank_main, args=(2, port, out), nprocs=2, join=True, start_method="spawn")
+    prm, X, P, N = _adjoint_case()
+    gx, gp, gh, ge, _, PN = oracle.gradient(prm, X, P, N)
+    L = oracle.loss_variance(PN)
+    for rank in range(2):
+        r0, cnt = shard.row_band(X.shape[1], rank, 2)
+        got = np.load(out + f".{rank}.npy")
+        np.testing.assert_allclose(got[:3], [L, gh, ge], rtol=1e-12)
+        np.testing.assert_allclose(got[3:3 + 3 * cnt].reshape(3, cnt), gx[:, r0:r0 + cnt], rtol=1e-12, atol=1e-15)
+        np.testing.assert_allclose(got[3 + 3 * cnt:].reshape(3, cnt), gp[:, r0:r0 + cnt], rtol=1e-12, atol=1e-15)
+
+
+def test_sharded_loss_merge_any_split():
+    """Loss partials merged in rank order give the whole ensemble's mean, variance
+    and loss for uneven splits, including an empty shard."""
+    rng = np.random.default_rng(5)
+    P = rng.normal(10.0, 3.0, (3, 1001))
+    whole = shard.combine_loss([shard.loss_partials(P)])
+    for cuts in ([0, 1, 500, 1001], [0, 0, 1001], [0, 333, 334, 1001]):
+        parts = [shard.loss_partials(P[:, a:b]) for a, b in zip(cuts[:-1], cuts[1:])]
+        c = shard.combine_loss(parts)
+        assert c["n"] == 1001
+        np.testing.assert_allclose(c["mean"], whole["mean"], rtol=1e-14)
+        np.testing.assert_allclose(c["var"], whole["var"], rtol=1e-12)
+        assert abs(c["loss"] - oracle.loss_variance(P)) <= 1e-12 * abs(c["loss"])
