@@ -145,9 +145,15 @@ def cpu_oracle_rate(seconds: float, cells: int = 512):
     t0 = time.perf_counter()
     st.advance(steps, threads=cores)
     dt = time.perf_counter() - t0
+    # the same oracle on one thread, over a short sample of the same cells
+    one = oracle.State(X[:, :32].copy(), P[:, :32].copy(), oracle.Params(eps=EPS, h=H, renorm_every=100))
+    t1 = time.perf_counter()
+    one.advance(400)
+    single = 32 * 400 / (time.perf_counter() - t1)
     return {"value": cells * steps / dt, "unit": "map-steps/s", "cores": cores, "kind": "oracle",
+            "single_thread": single,
             "sample": f"{cells} sampled cells of the 2048x2048 E=400 grid x {steps} composite steps "
-                      f"(tangent on), FP64, {dt:.1f} s"}
+                      f"(tangent on), FP64, {dt:.1f} s; single_thread: 32 of those cells x 400 steps on one thread"}
 
 
 def run_reference(args, rank: int):
@@ -274,6 +280,8 @@ def main():
                 "issued_instr_per_map_step_ncu": FP64_ISSUED_PER_STEP_NCU,
                 "issue_frac": (map_steps_per_launch / (per_launch_ms * 1e-3) * FP64_ISSUED_PER_STEP_NCU / ffma
                                if FP64_ISSUED_PER_STEP_NCU else None)}
+    tr = roofline["traffic"]
+    roofline["dram_gbs"] = tr / (per_launch_ms * 1e-3) / 1e9 if tr else None   # measured bytes / launch time
 
     # ---- end to end through the C ABI with host buffers (pinned) ----
     e2e = None
