@@ -119,13 +119,14 @@ __host__ __device__ __forceinline__ int clz64(unsigned long long v) {
 __host__ __device__ __forceinline__ void reduce_pair(double x, double t, float& rh, float& rl) {
   const unsigned long long bx = f64_bits(x), bt = f64_bits(t);
   const int ex = (int)((bx >> 52) & 0x7FFu), et = (int)(bt >> 52);
-  const long long mx0 = (long long)((bx & 0xFFFFFFFFFFFFFULL) | (ex ? 0x10000000000000ULL : 0ULL));
-  const long long mx = (bx >> 63) ? -mx0 : mx0;
-  const long long mt = (long long)((bt & 0xFFFFFFFFFFFFFULL) | (et ? 0x10000000000000ULL : 0ULL));
+  const unsigned long long mx = (bx & 0xFFFFFFFFFFFFFULL) | (ex ? 0x10000000000000ULL : 0ULL);
+  const unsigned long long mt = (bt & 0xFFFFFFFFFFFFFULL) | (et ? 0x10000000000000ULL : 0ULL);
   const int ex1 = ex ? ex : 1, et1 = et ? et : 1;    // subnormals share the exponent of 2^-1022
   const int e0 = (mt == 0 || ex1 < et1) ? ex1 : et1;
   const int sx = ex1 - e0, st = et1 - e0;          // 0..2 when both are non-zero
-  const long long R = (mx << (sx < 8 ? sx : 8)) - (mt == 0 ? 0LL : (mt << (st < 8 ? st : 8)));
+  // magnitudes shifted as unsigned (< 2^61), then signed
+  const long long ax = (long long)(mx << (sx < 8 ? sx : 8));
+  const long long R = ((bx >> 63) ? -ax : ax) - (mt == 0 ? 0LL : (long long)(mt << (st < 8 ? st : 8)));
   const unsigned int sign = R < 0 ? 0x80000000u : 0u;
   const unsigned long long U = (unsigned long long)(R < 0 ? -R : R);
   const int lz = clz64(U);
