@@ -151,11 +151,12 @@ def main(argv=None):
     args = sys.argv[1:] if argv is None else argv
     if not args or args[0] != "sweep":
         raise SystemExit("usage: python -m paper_1107_4107_b300.experiments sweep")
-    for prec in ("fp64", "fp32c"):
+    steps = {"fp64": (200, 50), "fp32c": (1000, 400), "df64": (400, 100)}   # (N <= 606,208, larger N)
+    for prec in ("fp64", "fp32c", "df64"):
         small = [n for n in SWEEP_NS if n <= 606208]
         big = [n for n in SWEEP_NS if n > 606208]
-        rows = throughput_vs_n(small, steps=200 if prec == "fp64" else 1000, precision=prec)
-        rows += throughput_vs_n(big, steps=50 if prec == "fp64" else 400, precision=prec)
+        rows = throughput_vs_n(small, steps=steps[prec][0], precision=prec)
+        rows += throughput_vs_n(big, steps=steps[prec][1], precision=prec)
         for r in rows:
             r["precision"] = prec
             print(json.dumps(r), flush=True)
