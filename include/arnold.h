@@ -48,7 +48,7 @@ extern "C" {
 #define ARNOLD_ENONFINITE   -5  /* the state became NaN/Inf (checked when results are read)         */
 #define ARNOLD_EUNSUPPORTED -6  /* combination not built (e.g. no CUDA device)                      */
 #define ARNOLD_ESTATE       -7  /* call out of order (e.g. arnold_grad before arnold_forward_ckpt)  */
-#define ARNOLD_ERANGE       -8  /* outside the precision mode's range (DF64: h |q| > 9 per step)    */
+#define ARNOLD_ERANGE       -8  /* outside the precision mode's range (h |q| per step > 9 for DF64, > 400 for FP32C) */
 
 /* ---- enums --------------------------------------------------------------- */
 /* Integrators (Sec. III names a sixth-order symplectic scheme whose reference
@@ -57,8 +57,10 @@ extern "C" {
 #define ARNOLD_SCHEME_TRIPLEJUMP6 1  /* recursive triple jump, 6th order, 9 kicks/step   */
 #define ARNOLD_SCHEME_LEAPFROG2   2  /* drift-kick-drift leapfrog, 2nd order, 1 kick/step */
 
-#define ARNOLD_FP64  0  /* state, tangent and sincos in FP64 (the paper used double precision, Sec. III) */
-#define ARNOLD_FP32C 1  /* compensated FP32: two-sum angle/action updates, FP64 angle reduction and logs   */
+#define ARNOLD_FP64  0  /* state, tangent and sincos to FP64 accuracy (the paper used double precision,
+                           Sec. III); FP64 instructions only where that accuracy needs them             */
+#define ARNOLD_FP32C 1  /* compensated FP32: float-pair angles (held in a [1024, 2048) rad window, whole
+                           turns removed exactly) and momenta, two-sum updates; FP64 logs and energy     */
 #define ARNOLD_DF64  2  /* double-float: state and kicks in float pairs (~48-bit), FP64-grade trajectories
                            on the FP32 pipes; tangent in FP32.  No adjoint or batch.                   */
 

@@ -182,11 +182,11 @@ __global__ void __launch_bounds__(256) k_adjoint_fp32c(AdjArgs a, Tab32 tb) {
     // pass 1: the state after every step of the segment
 #pragma unroll 1
     for (int s = 0; s < a.steps; ++s) {
-      drift32<false>(t, a.cf.sig_hi[0], a.cf.sig_lo[0]);
+      drift32<false, true>(t, a.cf.sig_hi[0], a.cf.sig_lo[0]);
 #pragma unroll
       for (int k = 0; k < M; ++k) {
         kick32<false>(t, a.cf.k2f[k], ssc, tb);
-        drift32<false>(t, a.cf.sig_hi[k + 1], a.cf.sig_lo[k + 1]);
+        drift32<false, true>(t, a.cf.sig_hi[k + 1], a.cf.sig_lo[k + 1]);
       }
       end_step32<false>(t, tb);
       float* sg = a.seg32 + (long long)s * 12 * n;
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(256) k_adjoint_fp32c(AdjArgs a, Tab32 tb) {
         lqu = fmaf(a.cf.sig_hi[k], lu, lqu);
         lqv = fmaf(a.cf.sig_hi[k], lv, lqv);
         lpz = fmaf(a.cf.sig_hi[k], lz, lpz);
-        drift32<false>(t, -a.cf.sig_hi[k], -a.cf.sig_lo[k]);
+        drift32<false, true>(t, -a.cf.sig_hi[k], -a.cf.sig_lo[k]);
         if (k > 0)
           adj_kick32(lu, lv, lz, lqu, lqv, lpz, t, a.cf.k2f[k - 1], a.cf.k4f[k - 1], a.chf[k - 1], a.cef[k - 1], gh,
                      ge, ssc, tb);

@@ -23,7 +23,9 @@ static long double round_bits(long double x, int bits) {
 }
 
 // FP32 table geometry (see Tab32 in step32.cuh): D = 2 pi / 2048 split into
-// d1 (7 significant bits) + d2 + d3, 2 pi split into c1 + c2 (18 bits each) + c3.
+// d1 (4 significant bits, so j d1 is exact for j < 2^20: angles below 3217
+// rad) + d2 + d3; 2 pi split into c1 (14 bits) + c2 (16 bits) + c3, so k c1
+// and k c2 are exact for |k| < 256 turns.
 // DF64 table geometry (TabDF in step_df.cuh): D = 2 pi / 2048 split d1 (11
 // significant bits) + d2 + d3; 2 pi split as for the FP32 table.
 void df_tab(TabDF* tb) {
@@ -48,7 +50,7 @@ void df_tab(TabDF* tb) {
 void fp32_tab(Tab32* tb) {
   const long double two_pi = 6.283185307179586476925286766559005768L;
   const long double D = two_pi / 2048.0L;
-  const long double d1 = round_bits(D, 7);
+  const long double d1 = round_bits(D, 4);
   const float d2 = (float)(D - d1);
   const float d3 = (float)(D - d1 - (long double)d2);
   tb->inv_d = (float)(1.0L / D);
@@ -57,8 +59,8 @@ void fp32_tab(Tab32* tb) {
   tb->d3 = d3;
   tb->jmax = 2047;
   tb->inv2pi = (float)(1.0L / two_pi);
-  const long double c1 = round_bits(two_pi, 18);
-  const long double c2 = round_bits(two_pi - c1, 18);
+  const long double c1 = round_bits(two_pi, 14);
+  const long double c2 = round_bits(two_pi - c1, 16);
   tb->c1 = (float)c1;
   tb->c2 = (float)c2;
   tb->c3 = (float)(two_pi - c1 - c2);
@@ -284,6 +286,10 @@ InitArgs init_args(arnold_ctx* c) {
   a.eps = c->prm.eps;
   a.tangent = c->prm.tangent;
   a.flags = c->flags;
+  if (c->prm.precision == ARNOLD_FP32C) {   // angles held in [kWinLo, kWinHi): 244 turns = 1533.1 rad
+    a.window_turns = 244;
+    fp32_tab(&a.tab32);
+  }
   return a;
 }
 

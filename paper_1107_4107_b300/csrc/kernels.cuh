@@ -1,6 +1,7 @@
 // Argument blocks and launchers of the set-up, read-out and statistics kernels.
 #pragma once
 #include "arnold_internal.cuh"
+#include "step32.cuh"
 
 namespace arnold {
 
@@ -19,6 +20,8 @@ struct InitArgs {
   unsigned long long seed;
   int tangent;
   int shell_mode;       // set_state: 0 P given, 1 P = |P| p (unit direction), 2 p_z from the energy
+  int window_turns;     // FP32C: whole turns added to each angle pair (into its window), laps debited
+  Tab32 tab32;          // FP32C: the 2 pi split used for those turns
   int* flags;
 };
 

@@ -96,8 +96,13 @@ __device__ __forceinline__ void renorm_sample32(const RunArgs32& a, long long i,
     const float inv = rsqrtf(n2);
     t.du *= inv; t.dv *= inv; t.dz *= inv;
     t.dqu *= inv; t.dqv *= inv; t.dpz *= inv;
-    if (!(n2 > 0.0f) || !isfinite(n2)) bad = 1;
+    if (!(n2 > 0.0f) || !isfinite(n2)) bad |= 1;
   }
+  // angles move at most h |q| within a step (the drift weights' partial sums stay in
+  // [0, 1]) and each drift adds at most 0.8 h |q|: with h |q| <= 400 they stay in
+  // [624, 2448] rad, above every increment and inside the table's exact range
+  const float qmax = fmaxf(fmaxf(fabsf(t.qu.hi), fabsf(t.qv.hi)), fabsf(t.pz.hi));
+  if (qmax * fabsf((float)a.h) > 400.0f) bad |= 2;
   float su, cu, sv, cv, sz, cz;
   sincos_tab32(t.u, ssc, tb, su, cu);
   sincos_tab32(t.v, ssc, tb, sv, cv);
@@ -106,7 +111,7 @@ __device__ __forceinline__ void renorm_sample32(const RunArgs32& a, long long i,
   const double H = kin + a.eps * (double)((cu + cv) * (cz * cz));
   const double dE = fabs(H - a.s.e0[i]);
   demax = fmax(demax, dE);
-  if (!isfinite(dE)) bad = 1;
+  if (!isfinite(dE)) bad |= 1;
   if (a.s.left) {
     const double qu = (double)t.qu.hi + (double)t.qu.lo, qv = (double)t.qv.hi + (double)t.qv.lo;
     if (!inside_patch(0.5 * (qu + qv), 0.5 * (qu - qv), (double)t.pz.hi + (double)t.pz.lo, a.s.patch)) a.s.left[i] = 1;
@@ -151,13 +156,13 @@ __device__ __forceinline__ void run_traj32(const RunArgs32& a, const Coef32& cf,
 #pragma unroll 1
   for (int s = 0; s < nsteps; ++s) {
 #pragma unroll
-    for (int r = 0; r < TPT; ++r) drift32<TAN>(t[r], cf.sh[0], cf.sl[0]);
+    for (int r = 0; r < TPT; ++r) drift32<TAN, true>(t[r], cf.sh[0], cf.sl[0]);
 #pragma unroll
     for (int k = 0; k < M; ++k) {
 #pragma unroll
       for (int r = 0; r < TPT; ++r) kick32<TAN>(t[r], cf.k2[k], ssc, tb);
 #pragma unroll
-      for (int r = 0; r < TPT; ++r) drift32<TAN>(t[r], cf.sh[k + 1], cf.sl[k + 1]);
+      for (int r = 0; r < TPT; ++r) drift32<TAN, true>(t[r], cf.sh[k + 1], cf.sl[k + 1]);
     }
 #pragma unroll
     for (int r = 0; r < TPT; ++r) end_step32<R64>(t[r], tb);
@@ -178,7 +183,8 @@ __device__ __forceinline__ void run_traj32(const RunArgs32& a, const Coef32& cf,
 #pragma unroll
   for (int r = 0; r < TPT; ++r)
     if (valid & (1 << r)) store32<TAN>(a, idx[r], t[r], logsum[r], demax[r]);
-  if (bad) atomicOr(a.flags, kFlagNonFinite);
+  if (bad & 1) atomicOr(a.flags, kFlagNonFinite);
+  if (bad & 2) atomicOr(a.flags, kFlagRange);
 }
 
 }  // namespace arnold

@@ -46,12 +46,16 @@ __device__ __forceinline__ void init_common(const InitArgs& a, long long i, doub
     const double vals[6] = {u, v, z, qu, qv, pz};
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-      const float hi = __double2float_rn(vals[c]);
-      a.f.hi[c * n + i] = hi;
-      a.f.lo[c * n + i] = __double2float_rn(vals[c] - (double)hi);
+      Pair x;
+      x.hi = __double2float_rn(vals[c]);
+      x.lo = __double2float_rn(vals[c] - (double)x.hi);
+      if (c < 3 && a.window_turns) add_turns32(x, (float)a.window_turns, a.tab32);   // exact
+      a.f.hi[c * n + i] = x.hi;
+      a.f.lo[c * n + i] = x.lo;
     }
   }
-  a.s.lap[i] = lu; a.s.lap[n + i] = lv; a.s.lap[2 * n + i] = lz;
+  const int T = a.window_turns;   // laps debited for the turns added (0 unless FP32C)
+  a.s.lap[i] = lu - T; a.s.lap[n + i] = lv - T; a.s.lap[2 * n + i] = lz - T;
   a.s.lapref[i] = lu; a.s.lapref[n + i] = lv; a.s.lapref[2 * n + i] = lz;
   a.s.ref[i] = u; a.s.ref[n + i] = v; a.s.ref[2 * n + i] = z;
   a.s.e0[i] = e0;

@@ -39,13 +39,17 @@ __device__ __forceinline__ void add_comp(Pair& x, float inc) {
 }
 
 // x += s * q with s = (sh, sl), q a pair: exact leading product + cross terms.
+// FAST: the angle is known to outweigh the increment (|x.hi| >= |p|), as for
+// FP32C angles held in [kWinLo, kWinHi), so Fast2Sum is exact; otherwise TwoSum.
+template <bool FAST>
 __device__ __forceinline__ void drift_comp(Pair& x, float sh, float sl, const Pair& q) {
   const float p = __fmul_rn(sh, q.hi);
   float e = fmaf(sh, q.hi, -p);          // exact error of the product
   e = fmaf(sh, q.lo, e);
   e = fmaf(sl, q.hi, e);
   float s, t;
-  two_sum(x.hi, p, s, t);
+  if (FAST) fast_two_sum(x.hi, p, s, t);
+  else two_sum(x.hi, p, s, t);
   x.hi = s;
   x.lo = __fadd_rn(x.lo, __fadd_rn(t, e));
 }
@@ -82,53 +86,64 @@ __device__ __forceinline__ void sincos_tab32(const Pair& x, const float2* __rest
   c = fmaf(-e.x, r, fmaf(e.y, cm, e.y));
 }
 
-// Exact removal of k = rint(x / 2 pi) turns from an angle pair, laps += k.
-// hi - k C1 and k C2 are exact (|k| < 64), the TwoSum keeps the second
-// subtraction exact, so the only rounding is at the level of lo.
-// REDUCE64 variant: the same in FP64 (widen, subtract k * 2pi, split).
+// FP32C angles are held in the window [kWinLo, kWinHi) rad (any angle is
+// one modulo 2 pi): there every angle outweighs its drift increment (|s q| <
+// 400 per step, checked at renormalisation), so drifts add with Fast2Sum, and
+// the table sincos stays exact (j d1 exact below 3217 rad).  An angle that
+// leaves the window is brought back near kWinMid by whole turns.
+constexpr float kWinLo = 1024.0f, kWinHi = 2048.0f, kWinMid = 1536.0f;
+
+// x += k * 2 pi exactly, 2 pi = C1 + C2 + C3 (14, 16 bits and the rest), |k| < 256:
+// k C1 and k C2 are exact products, two TwoSums keep both additions exact, so
+// the only rounding is at the level of lo.
+__device__ __forceinline__ void add_turns32(Pair& x, float kf, const Tab32& tb) {
+  float s, e, s2, e2;
+  two_sum(x.hi, __fmul_rn(kf, tb.c1), s, e);
+  two_sum(s, __fmul_rn(kf, tb.c2), s2, e2);
+  const float lo = fmaf(kf, tb.c3, __fadd_rn(__fadd_rn(x.lo, e), e2));
+  fast_two_sum(s2, lo, x.hi, x.lo);
+}
+
+// Bring an angle pair back to within pi of kWinMid, laps -= k for the k turns
+// added.  REDUCE64 variant: the same in FP64 (widen, add k * 2pi, split).
 template <bool REDUCE64>
 __device__ __forceinline__ void reduce_angle(Pair& x, int& lap, const Tab32& tb) {
   if (REDUCE64) {
     const double d = (double)x.hi + (double)x.lo;
-    const double k = rint(d * (1.0 / kTwoPi));
-    const double r = fma(-k, kTwoPi, d);
+    const double k = rint(((double)kWinMid - d) * (1.0 / kTwoPi));
+    const double r = fma(k, kTwoPi, d);
     x.hi = __double2float_rn(r);
     x.lo = __double2float_rn(r - (double)x.hi);
-    lap += (int)k;
+    lap -= (int)k;
   } else {
-    const float t = fmaf(x.hi, tb.inv2pi, 12582912.0f);
+    const float t = fmaf(__fsub_rn(kWinMid, x.hi), tb.inv2pi, 12582912.0f);   // kWinMid - hi: exact
     const float kf = __fsub_rn(t, 12582912.0f);
-    const int k = __float_as_int(t) - 0x4B400000;
-    const float h1 = fmaf(-kf, tb.c1, x.hi);
-    float s, e;
-    two_sum(h1, __fmul_rn(-kf, tb.c2), s, e);
-    const float lo = fmaf(-kf, tb.c3, __fadd_rn(x.lo, e));
-    fast_two_sum(s, lo, x.hi, x.lo);
-    lap += k;
+    add_turns32(x, kf, tb);
+    lap -= __float_as_int(t) - 0x4B400000;
   }
 }
 
-// End of a composite step: renormalise all pairs; reduce the angles once any
-// of them has grown past 64 rad (every few tens of steps at E = 400), which
-// keeps every kick's argument within the table's exact range for h |q| < 300.
 template <bool REDUCE64>
 __device__ __forceinline__ void end_step32(Traj32& t, const Tab32& tb) {
   renorm(t.u); renorm(t.v); renorm(t.z);
   renorm(t.qu); renorm(t.qv); renorm(t.pz);
-  const int big = max(max(__float_as_int(t.u.hi) & 0x7FFFFFFF, __float_as_int(t.v.hi) & 0x7FFFFFFF),
-                      __float_as_int(t.z.hi) & 0x7FFFFFFF);
-  if (big > 0x42800000) {   // |angle| > 64
+  // outside [kWinLo, kWinHi): (bits - bits(1024)) as unsigned >= bits(2048) - bits(1024)
+  const unsigned int lo_bits = 0x44800000u, span = 0x00800000u;
+  const bool out = (unsigned int)(__float_as_int(t.u.hi) - lo_bits) >= span ||
+                   (unsigned int)(__float_as_int(t.v.hi) - lo_bits) >= span ||
+                   (unsigned int)(__float_as_int(t.z.hi) - lo_bits) >= span;
+  if (out) {
     reduce_angle<REDUCE64>(t.u, t.lu, tb);
     reduce_angle<REDUCE64>(t.v, t.lv, tb);
     reduce_angle<REDUCE64>(t.z, t.lz, tb);
   }
 }
 
-template <bool TAN>
+template <bool TAN, bool FAST = false>
 __device__ __forceinline__ void drift32(Traj32& t, float sh, float sl) {
-  drift_comp(t.u, sh, sl, t.qu);
-  drift_comp(t.v, sh, sl, t.qv);
-  drift_comp(t.z, sh, sl, t.pz);
+  drift_comp<FAST>(t.u, sh, sl, t.qu);
+  drift_comp<FAST>(t.v, sh, sl, t.qv);
+  drift_comp<FAST>(t.z, sh, sl, t.pz);
   if (TAN) {
     t.du = fmaf(sh, t.dqu, t.du);
     t.dv = fmaf(sh, t.dqv, t.dv);

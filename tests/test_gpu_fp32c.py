@@ -155,3 +155,24 @@ def test_fp32c_full_size_grid_sampled_cells():
         k = int(np.argmax(err / bar))
         print(f"worst cell: err {err[k]:.2e}, growth {growth[k]:.2f}, bar {bar[k]:.2e}")
         assert np.all(err <= bar)
+
+
+def test_fp32c_range_is_reported():
+    """FP32C holds angles in a [1024, 2048) rad window, valid while an angle moves
+    at most 400 rad per step (h |q| <= 400): beyond that the run reports ERANGE at
+    the next renormalisation (the table index stays masked, so nothing is read out
+    of bounds meanwhile)."""
+    from paper_1107_4107_b300._lib import ERANGE
+    from paper_1107_4107_b300.api import ArnoldError
+    X, P = inputs.box(64, seed=61)
+    P[0] *= 50.0                          # |q| ~ 500 at h = 1: 500 rad per step
+    e = _ens(64, precision="fp32c", h=1.0, renorm_every=5)
+    e.set_state(X, P)
+    e.iterate(10)
+    with pytest.raises(ArnoldError) as ex:
+        e.sync()
+    assert ex.value.status == ERANGE
+    ok = _ens(64, precision="fp32c", h=0.05, renorm_every=5)
+    ok.set_state(*inputs.box(64, seed=61))
+    ok.iterate(10)
+    ok.sync()
