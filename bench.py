@@ -46,12 +46,12 @@ FP64_INSTR_PER_STEP = 7 * (3 * 2 + 7 + 13) + 8 * 6
 FP64_FLOP_PER_STEP = 7 * (3 * 2 + 10 + 20) + 8 * 12
 # FP32C: FP32/INT arithmetic per composite step counted from the source
 # (step32.cuh): kick = 3 sincos (12 each) + force with TwoSum adds (4 + 3 +
-# 3 * 7) + tangent (14); drift = 3 * (4 product + 6 TwoSum + 2) + 3 tangent;
-# end of step = 6 Fast2Sum renormalisations + the reduction test.
-FP32C_INSTR_PER_STEP = 7 * (3 * 12 + 28 + 14) + 8 * (3 * 12 + 3) + 6 * 3 + 6
+# 3 * 7) + tangent (14); drift = 3 * (4 product + 3 Fast2Sum + 2) + 3 tangent;
+# end of step = 6 Fast2Sum renormalisations + the window test.
+FP32C_INSTR_PER_STEP = 7 * (3 * 12 + 28 + 14) + 8 * (3 * 9 + 3) + 6 * 3 + 6
 # Measured by ncu for k_iterate_fp32c<7,true,false> (all pipes, per map step):
 # profiles/k_iterate_fp32c__grid2048_E400_1M_traj_400_steps.md
-FP32C_ISSUED_PER_STEP_NCU = 1018
+FP32C_ISSUED_PER_STEP_NCU = 956
 # Measured by ncu for k_iterate_fp64<7,true> (all pipes: FP64, FP32, INT, LSU):
 # profiles/k_iterate_fp64__grid2048_E400_1M_traj_20_steps.md
 FP64_ISSUED_PER_STEP_NCU = 8018
