@@ -21,13 +21,13 @@ struct RunArgs32 {
 
 // Step coefficients of one ensemble in FP32 (drifts as float pairs).
 struct Coef32 {
-  float sh[10], sl[10], k2[9], k4[9];
+  float sh[10], sl[10], k2[9];
 };
 
 __host__ __device__ inline Coef32 coef32_from(const StepCoef& c) {
   Coef32 r;
   for (int k = 0; k < 10; ++k) { r.sh[k] = c.sig_hi[k]; r.sl[k] = c.sig_lo[k]; }
-  for (int k = 0; k < 9; ++k) { r.k2[k] = c.k2f[k]; r.k4[k] = c.k4f[k]; }
+  for (int k = 0; k < 9; ++k) r.k2[k] = c.k2f[k];
   return r;
 }
 
