@@ -144,13 +144,54 @@ SWEEP_NS = [1, 32, 148, 1024, 4736, 9472, 9473, 18944, 37888, 75776, 151552, 151
             4194304, 10000000]
 
 
+def timed_web_experiment(n: int, E: float = 400.0, window_T: float = 50.0, precision: str = "fp64",
+                         n_cos: int = 256, n_phi: int = 512, seed: int = 0, device: int = 0) -> dict:
+    """One web experiment of Sec. IV at a given scale (the paper's: N ~ 1e8, t_p =
+    dt = 50 T = 5000 steps, FP64): sphere ICs, propagation, F.  Returns the
+    host set-up time, the propagation time (CUDA events on the ensemble's
+    stream) and the histogram time."""
+    import time
+
+    import torch
+    h = paper_h()
+    steps = int(round(window_T * T / h))
+    st = torch.cuda.current_stream(device)
+    t0 = time.perf_counter()
+    e = ArnoldEnsemble(n, precision=precision, tangent=False, h=h, window=steps, device=device,
+                       stream=st.cuda_stream)
+    e.init_sphere(E, seed=seed)
+    e.sync()
+    t_init = time.perf_counter() - t0
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    e.iterate(steps)
+    b.record(st)
+    b.synchronize()
+    e.sync()
+    t_prop = a.elapsed_time(b) * 1e-3
+    t1 = time.perf_counter()
+    counts = e.velocity_histogram(n_cos, n_phi)
+    t_hist = time.perf_counter() - t1
+    e.close()
+    return {"n": n, "E": E, "steps": steps, "precision": precision, "init_s": t_init, "propagate_s": t_prop,
+            "map_steps_per_s": n * steps / t_prop, "histogram_s": t_hist, "counted": int(counts.sum())}
+
+
 def main(argv=None):
-    """python -m paper_1107_4107_b300.experiments sweep   -> JSON lines of throughput_vs_n."""
+    """python -m paper_1107_4107_b300.experiments sweep
+           -> JSON lines of throughput_vs_n
+       python -m paper_1107_4107_b300.experiments web N PRECISION [E]
+           -> one timed web experiment (sphere, 5000 steps, F) as a JSON line"""
     import json
     import sys
     args = sys.argv[1:] if argv is None else argv
+    if args and args[0] == "web" and len(args) >= 3:
+        r = timed_web_experiment(int(float(args[1])), E=float(args[3]) if len(args) > 3 else 400.0,
+                                 precision=args[2])
+        print(json.dumps(r), flush=True)
+        return
     if not args or args[0] != "sweep":
-        raise SystemExit("usage: python -m paper_1107_4107_b300.experiments sweep")
+        raise SystemExit("usage: python -m paper_1107_4107_b300.experiments sweep | web N PRECISION [E]")
     steps = {"fp64": (200, 50), "fp32c": (1000, 400), "df64": (400, 100)}   # (N <= 606,208, larger N)
     for prec in ("fp64", "fp32c", "df64"):
         small = [n for n in SWEEP_NS if n <= 606208]
