@@ -177,21 +177,50 @@ def timed_web_experiment(n: int, E: float = 400.0, window_T: float = 50.0, preci
             "map_steps_per_s": n * steps / t_prop, "histogram_s": t_hist, "counted": int(counts.sum())}
 
 
+def timed_diffusion_rate(n: int = 32000, E: float = 15.0, steps: int = 50000, precision: str = "fp64",
+                         sigma: float = 0.01, seed: int = 0, device: int = 0) -> dict:
+    """Rate of the long diffusion run of Fig. 4 (the cloud at W, no tangent) over
+    `steps` steps, and the projected time of the paper's 1e9 steps at that rate."""
+    import torch
+    st = torch.cuda.current_stream(device)
+    e = init_gaussian_valid(n, E, (math.sqrt(E), math.sqrt(E)), sigma, seed, precision=precision,
+                            window=int(round(50 * T / paper_h())), device=device, stream=st.cuda_stream)
+    e.iterate(100)                       # warm-up
+    e.sync()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    e.iterate(steps)
+    b.record(st)
+    b.synchronize()
+    e.sync()
+    sec = a.elapsed_time(b) * 1e-3
+    rate = n * steps / sec
+    e.close()
+    return {"n": n, "E": E, "steps": steps, "precision": precision, "seconds": sec, "map_steps_per_s": rate,
+            "projected_1e9_steps_h": n * 1e9 / rate / 3600.0}
+
+
 def main(argv=None):
     """python -m paper_1107_4107_b300.experiments sweep
            -> JSON lines of throughput_vs_n
        python -m paper_1107_4107_b300.experiments web N PRECISION [E]
-           -> one timed web experiment (sphere, 5000 steps, F) as a JSON line"""
+           -> one timed web experiment (sphere, 5000 steps, F) as a JSON line
+       python -m paper_1107_4107_b300.experiments diffusion PRECISION
+           -> the Fig. 4 diffusion run's rate (32,000 trajectories, E = 15)"""
     import json
     import sys
     args = sys.argv[1:] if argv is None else argv
+    if args and args[0] == "diffusion" and len(args) >= 2:
+        print(json.dumps(timed_diffusion_rate(precision=args[1])), flush=True)
+        return
     if args and args[0] == "web" and len(args) >= 3:
         r = timed_web_experiment(int(float(args[1])), E=float(args[3]) if len(args) > 3 else 400.0,
                                  precision=args[2])
         print(json.dumps(r), flush=True)
         return
     if not args or args[0] != "sweep":
-        raise SystemExit("usage: python -m paper_1107_4107_b300.experiments sweep | web N PRECISION [E]")
+        raise SystemExit("usage: python -m paper_1107_4107_b300.experiments sweep | web N PRECISION [E] | "
+                         "diffusion PRECISION")
     steps = {"fp64": (200, 50), "fp32c": (1000, 400), "df64": (400, 100)}   # (N <= 606,208, larger N)
     for prec in ("fp64", "fp32c", "df64"):
         small = [n for n in SWEEP_NS if n <= 606208]
