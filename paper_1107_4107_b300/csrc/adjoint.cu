@@ -37,13 +37,14 @@ __device__ __forceinline__ void adj_kick64(double& lu, double& lv, double& lz, d
   const double g = cz * cz, sh = sz * cz;
   const double kc = k2 * cz;
   const double G = kc * cz, Sp = kc * sz, A = cu + cv;   // as the forward kick forms them
-  const double F = fma(lqu * su, g, fma(lqv * sv, g, lpz * (sh * A)));
+  const double sl = fma(su, lqu, sv * lqv);             // s_u lq_u + s_v lq_v, used twice
+  const double F = fma(g, sl, (sh * A) * lpz);
   gh = fma(ch, F, gh);
   ge = fma(ce, F, ge);
   const double Z = A * fma(k4, g, -k2);
   lu = fma(G * cu, lqu, fma(-Sp * su, lpz, lu));
   lv = fma(G * cv, lqv, fma(-Sp * sv, lpz, lv));
-  lz = fma(-2.0 * Sp, fma(su, lqu, sv * lqv), fma(Z, lpz, lz));
+  lz = fma(neg_times2(Sp), sl, fma(Z, lpz, lz));
   t.qu = fma(-G, su, t.qu);
   t.qv = fma(-G, sv, t.qv);
   t.pz = fma(-Sp, A, t.pz);
