@@ -19,9 +19,29 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--launches", type=int, default=3)
     ap.add_argument("--no-tangent", action="store_true")
+    ap.add_argument("--adjoint", type=int, default=0, metavar="C",
+                    help="instead: the FP64/FP32C adjoint of the variance loss over --steps steps of --n box "
+                         "trajectories with checkpoints every C steps (one k_adjoint launch per segment)")
     a = ap.parse_args()
     import torch
     from .api import ArnoldEnsemble
+    if a.adjoint:
+        from . import inputs
+        X, P = inputs.box(a.n, seed=0)
+        e = ArnoldEnsemble(a.n, precision=a.precision, tangent=False, stream=torch.cuda.current_stream().cuda_stream)
+        e.set_state(X, P)
+        e.forward_ckpt(a.steps, a.adjoint)
+        PN = torch.empty((3, a.n), device="cuda", dtype=torch.float64)
+        e.indicator("P", out=PN)
+        up = ((2.0 / 3.0) * (PN - PN.mean(dim=1, keepdim=True)) / a.n).contiguous()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        g = e.grad(dL_dp=up)
+        t1.record()
+        t1.synchronize()
+        print(json.dumps({"adjoint": a.precision, "n": a.n, "steps": a.steps, "ckpt_every": a.adjoint,
+                          "reverse_ms": t0.elapsed_time(t1), "dL_dh": float(g[2])}))
+        return
     G = 2048
     if a.n % G:
         raise SystemExit("--n must be a multiple of 2048")
