@@ -177,6 +177,39 @@ def timed_web_experiment(n: int, E: float = 400.0, window_T: float = 50.0, preci
             "map_steps_per_s": n * steps / t_prop, "histogram_s": t_hist, "counted": int(counts.sum())}
 
 
+def scan_agreement(E: float = 400.0, steps: int = 1_000_000, G: int = 2048, precisions=("fp64", "fp32c", "df64"),
+                   seed: int = 0, device: int = 0) -> list[dict]:
+    """The Arnold-web scan of Sec. IV on a G x G grid of initial actions at
+    energy E, run to `steps` steps in every precision mode from the same initial
+    conditions; per mode the time, chaotic fraction and, against the first mode,
+    class agreement and the L1 distance of the log10 chi histograms."""
+    import torch
+    st = torch.cuda.current_stream(device)
+    out, ref = [], None
+    for prec in precisions:
+        e = ArnoldEnsemble(G * G, precision=prec, device=device, stream=st.cuda_stream)
+        e.init_grid(G, E, seed=seed)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        e.iterate(steps)
+        b.record(st)
+        b.synchronize()
+        e.sync()
+        chi, cls = e.indicator("chi"), e.indicator("class")
+        r = {"precision": prec, "E": E, "G": G, "steps": steps, "seconds": a.elapsed_time(b) * 1e-3,
+             "map_steps_per_s": G * G * steps / (a.elapsed_time(b) * 1e-3), "chaotic_fraction": float(cls.mean()),
+             "dE_max": float(e.indicator("dE_max").max())}
+        if ref is None:
+            ref = (chi, cls)
+        else:
+            h = lambda c: np.histogram(np.log10(np.clip(c, 1e-300, None)), bins=200, range=(-8, 1))[0] / c.size
+            r["class_agreement"] = float(np.mean(cls == ref[1]))
+            r["hist_l1"] = float(np.abs(h(chi) - h(ref[0])).sum())
+        e.close()
+        out.append(r)
+    return out
+
+
 def timed_diffusion_rate(n: int = 32000, E: float = 15.0, steps: int = 50000, precision: str = "fp64",
                          sigma: float = 0.01, seed: int = 0, device: int = 0) -> dict:
     """Rate of the long diffusion run of Fig. 4 (the cloud at W, no tangent) over
@@ -206,10 +239,17 @@ def main(argv=None):
        python -m paper_1107_4107_b300.experiments web N PRECISION [E]
            -> one timed web experiment (sphere, 5000 steps, F) as a JSON line
        python -m paper_1107_4107_b300.experiments diffusion PRECISION
-           -> the Fig. 4 diffusion run's rate (32,000 trajectories, E = 15)"""
+           -> the Fig. 4 diffusion run's rate (32,000 trajectories, E = 15)
+       python -m paper_1107_4107_b300.experiments scan E STEPS [G]
+           -> the G x G scan in FP64, FP32C and DF64 with agreement vs FP64"""
     import json
     import sys
     args = sys.argv[1:] if argv is None else argv
+    if args and args[0] == "scan" and len(args) >= 3:
+        for r in scan_agreement(E=float(args[1]), steps=int(float(args[2])),
+                                G=int(args[3]) if len(args) > 3 else 2048):
+            print(json.dumps(r), flush=True)
+        return
     if args and args[0] == "diffusion" and len(args) >= 2:
         print(json.dumps(timed_diffusion_rate(precision=args[1])), flush=True)
         return
@@ -220,7 +260,7 @@ def main(argv=None):
         return
     if not args or args[0] != "sweep":
         raise SystemExit("usage: python -m paper_1107_4107_b300.experiments sweep | web N PRECISION [E] | "
-                         "diffusion PRECISION")
+                         "diffusion PRECISION | scan E STEPS [G]")
     steps = {"fp64": (200, 50), "fp32c": (1000, 400), "df64": (400, 100)}   # (N <= 606,208, larger N)
     for prec in ("fp64", "fp32c", "df64"):
         small = [n for n in SWEEP_NS if n <= 606208]

@@ -35,3 +35,15 @@ def test_diffusion_resume_equals_uninterrupted(tmp_path):
     rest = diffusion_from_w(**kw, ckpt_path=ck)
     assert np.array_equal(part["maps"][0]["counts"], full["maps"][0]["counts"])
     assert np.array_equal(rest["maps"][0]["counts"], full["maps"][1]["counts"])
+
+
+def test_scan_agreement_runs_all_modes_from_the_same_ics():
+    """The precision-comparison scan: every mode runs from the same grid ICs; the
+    FP64 mode is the reference, the others report class agreement and histogram L1
+    (short horizon: near-identical classes)."""
+    from paper_1107_4107_b300.experiments import scan_agreement
+    rows = scan_agreement(E=40.0, steps=300, G=64)
+    assert [r["precision"] for r in rows] == ["fp64", "fp32c", "df64"]
+    for r in rows[1:]:
+        assert r["class_agreement"] >= 0.99 and r["hist_l1"] <= 1e-2
+    assert all(r["map_steps_per_s"] > 0 for r in rows)
