@@ -253,7 +253,7 @@ void free_all(arnold_ctx* c) {
   void* ptrs[] = {c->s.st, c->s.tg, c->s.lap, c->s.lapref, c->s.ref, c->s.logsum, c->s.demax, c->s.e0, c->s.V,
                   c->f.hi, c->f.lo, c->f.tg, c->sc, c->th, c->scf, c->scd, c->flags, c->partials, c->stats_out,
                   c->scratch, c->scratch2, c->ck, c->seg, c->lam, c->lamf, c->gh, c->ge, c->sum_part, c->s.left,
-                  c->vhist, c->s.megno};
+                  c->vhist, c->s.megno, c->f.tg_lo};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -411,6 +411,7 @@ int arnold_create(const arnold_params* prm, int64_t n_traj, int device, void* cu
     e = dalloc(&c->f.hi, 6 * n);
     if (e == cudaSuccess) e = dalloc(&c->f.lo, 6 * n);
     if (e == cudaSuccess && tan) e = dalloc(&c->f.tg, 6 * n);
+    if (e == cudaSuccess && tan && prm->precision == ARNOLD_DF64) e = dalloc(&c->f.tg_lo, 6 * n);
   }
   if (e == cudaSuccess) e = dalloc(&c->s.lap, 3 * n);
   if (e == cudaSuccess) e = dalloc(&c->s.lapref, 3 * n);
@@ -861,6 +862,7 @@ static int ckpt_arrays(const arnold_ctx* c, void** ptrs, size_t* sizes) {
   add(c->f.hi, 24 * n);
   add(c->f.lo, 24 * n);
   add(c->f.tg, 24 * n);
+  add(c->f.tg_lo, 24 * n);
   add(c->s.lap, 12 * n);
   add(c->s.lapref, 12 * n);
   add(c->s.ref, 24 * n);

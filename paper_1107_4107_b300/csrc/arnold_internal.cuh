@@ -99,7 +99,8 @@ __device__ __forceinline__ bool inside_patch(double px, double py, double pz, co
 struct Fp32cState {
   float* hi;       // [6][n] u, v, z, q_u, q_v, p_z (leading parts)
   float* lo;       // [6][n] trailing parts (value = hi + lo)
-  float* tg;       // [6][n] tangent in FP32
+  float* tg;       // [6][n] tangent in FP32 (DF64: the leading words)
+  float* tg_lo;    // [6][n] DF64 only: trailing words of the double-float tangent (null otherwise)
 };
 
 struct IterArgs {

@@ -41,34 +41,59 @@ __global__ void __launch_bounds__(256) k_iterate_df64(IterArgs a, TabDF tb, Coef
   ra.flags = a.flags;
   const float hf = (float)a.h;
   const long long n = a.n;
+  auto pd = [](const Pair& p) { return (double)p.hi + (double)p.lo; };
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    Traj32 t;
-    double logsum, demax;
-    load32<TAN>(ra, i, t, logsum, demax);
+    TrajDF t;
+    t.u = {a.f.hi[i], a.f.lo[i]};
+    t.v = {a.f.hi[n + i], a.f.lo[n + i]};
+    t.z = {a.f.hi[2 * n + i], a.f.lo[2 * n + i]};
+    t.qu = {a.f.hi[3 * n + i], a.f.lo[3 * n + i]};
+    t.qv = {a.f.hi[4 * n + i], a.f.lo[4 * n + i]};
+    t.pz = {a.f.hi[5 * n + i], a.f.lo[5 * n + i]};
+    if (TAN) {
+      t.du = {a.f.tg[i], a.f.tg_lo[i]};
+      t.dv = {a.f.tg[n + i], a.f.tg_lo[n + i]};
+      t.dz = {a.f.tg[2 * n + i], a.f.tg_lo[2 * n + i]};
+      t.dqu = {a.f.tg[3 * n + i], a.f.tg_lo[3 * n + i]};
+      t.dqv = {a.f.tg[4 * n + i], a.f.tg_lo[4 * n + i]};
+      t.dpz = {a.f.tg[5 * n + i], a.f.tg_lo[5 * n + i]};
+    }
+    t.lu = a.s.lap[i];
+    t.lv = a.s.lap[n + i];
+    t.lz = a.s.lap[2 * n + i];
+    double logsum = TAN ? a.s.logsum[i] : 0.0;
+    double demax = a.s.demax[i];
     int to_renorm = a.R - (int)(a.step0 % a.R);
     long long to_window = a.W > 0 ? a.W - a.step0 % a.W : 0;
     int bad = 0;
 #pragma unroll 1
     for (int s = 0; s < a.nsteps; ++s) {
-      drift32<TAN>(t, cf.sh[0], cf.sl[0]);
+      drift_df<TAN>(t, cf.sh[0], cf.sl[0]);
 #pragma unroll 1
       for (int k = 0; k < M; ++k) {
         kick_df<TAN>(t, cf.k2[k], stab, tb);
-        drift32<TAN>(t, cf.sh[k + 1], cf.sl[k + 1]);
+        drift_df<TAN>(t, cf.sh[k + 1], cf.sl[k + 1]);
       }
-      end_step_df(t, tb);
+      end_step_df<TAN>(t, tb);
       if (--to_renorm == 0) {
         to_renorm = a.R;
-        if (TAN) {
-          const float n2 = 0.5f * (t.du * t.du + t.dv * t.dv) + t.dz * t.dz +
-                           0.5f * (t.dqu * t.dqu + t.dqv * t.dqv) + t.dpz * t.dpz;
-          const double l = 0.5 * (double)__logf(n2);
+        if (TAN) {   // norm and log in FP64 (once per R steps)
+          const double w0 = pd(t.du), w1 = pd(t.dv), w2 = pd(t.dz), w3 = pd(t.dqu), w4 = pd(t.dqv), w5 = pd(t.dpz);
+          const double n2 = 0.5 * (w0 * w0 + w1 * w1) + w2 * w2 + 0.5 * (w3 * w3 + w4 * w4) + w5 * w5;
+          const double l = 0.5 * log(n2);
           logsum += l;
           if (a.s.megno) megno_update(a.s.megno, n, i, (a.step0 + s + 1) / a.R, l);
-          const float inv = rsqrtf(n2);
-          t.du *= inv; t.dv *= inv; t.dz *= inv;
-          t.dqu *= inv; t.dqv *= inv; t.dpz *= inv;
-          if (!(n2 > 0.0f) || !isfinite(n2)) bad = 1;
+          // rescale (the next log measures the norm actually left, so the
+          // rounding of the factor does not accumulate)
+          const float inv = rsqrtf(__double2float_rn(n2));
+          Pair* w[6] = {&t.du, &t.dv, &t.dz, &t.dqu, &t.dqv, &t.dpz};
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            const float p = __fmul_rn(w[c]->hi, inv);
+            const float e = fmaf(w[c]->lo, inv, fmaf(w[c]->hi, inv, -p));
+            fast_two_sum(p, e, w[c]->hi, w[c]->lo);
+          }
+          if (!(n2 > 0.0) || !isfinite(n2)) bad = 1;
         }
         const double kin = 0.25 * (pair_sq_d(t.qu) + pair_sq_d(t.qv)) + 0.5 * pair_sq_d(t.pz);
         const double dE = fabs(kin + a.eps * potential_df(t, stab, tb) - a.s.e0[i]);
@@ -80,9 +105,8 @@ __global__ void __launch_bounds__(256) k_iterate_df64(IterArgs a, TabDF tb, Coef
         const float qmax = fmaxf(fmaxf(fabsf(t.qu.hi), fabsf(t.qv.hi)), fabsf(t.pz.hi));
         if (qmax * fabsf(hf) > 9.0f) atomicOr(a.flags, kFlagRange);
         if (a.s.left) {
-          const double qu = (double)t.qu.hi + (double)t.qu.lo, qv = (double)t.qv.hi + (double)t.qv.lo;
-          if (!inside_patch(0.5 * (qu + qv), 0.5 * (qu - qv), (double)t.pz.hi + (double)t.pz.lo, a.s.patch))
-            a.s.left[i] = 1;
+          const double qu = pd(t.qu), qv = pd(t.qv);
+          if (!inside_patch(0.5 * (qu + qv), 0.5 * (qu - qv), pd(t.pz), a.s.patch)) a.s.left[i] = 1;
         }
       }
       if (a.W > 0 && --to_window == 0) {
@@ -90,7 +114,25 @@ __global__ void __launch_bounds__(256) k_iterate_df64(IterArgs a, TabDF tb, Coef
         close_window32(ra, i, t, (a.step0 + s + 1) / a.W);
       }
     }
-    store32<TAN>(ra, i, t, logsum, demax);
+    a.f.hi[i] = t.u.hi;          a.f.lo[i] = t.u.lo;
+    a.f.hi[n + i] = t.v.hi;      a.f.lo[n + i] = t.v.lo;
+    a.f.hi[2 * n + i] = t.z.hi;  a.f.lo[2 * n + i] = t.z.lo;
+    a.f.hi[3 * n + i] = t.qu.hi; a.f.lo[3 * n + i] = t.qu.lo;
+    a.f.hi[4 * n + i] = t.qv.hi; a.f.lo[4 * n + i] = t.qv.lo;
+    a.f.hi[5 * n + i] = t.pz.hi; a.f.lo[5 * n + i] = t.pz.lo;
+    if (TAN) {
+      a.f.tg[i] = t.du.hi;          a.f.tg_lo[i] = t.du.lo;
+      a.f.tg[n + i] = t.dv.hi;      a.f.tg_lo[n + i] = t.dv.lo;
+      a.f.tg[2 * n + i] = t.dz.hi;  a.f.tg_lo[2 * n + i] = t.dz.lo;
+      a.f.tg[3 * n + i] = t.dqu.hi; a.f.tg_lo[3 * n + i] = t.dqu.lo;
+      a.f.tg[4 * n + i] = t.dqv.hi; a.f.tg_lo[4 * n + i] = t.dqv.lo;
+      a.f.tg[5 * n + i] = t.dpz.hi; a.f.tg_lo[5 * n + i] = t.dpz.lo;
+      a.s.logsum[i] = logsum;
+    }
+    a.s.lap[i] = t.lu;
+    a.s.lap[n + i] = t.lv;
+    a.s.lap[2 * n + i] = t.lz;
+    a.s.demax[i] = demax;
     if (bad) atomicOr(a.flags, kFlagNonFinite);
   }
 }

@@ -120,7 +120,8 @@ __device__ __forceinline__ void renorm_sample32(const RunArgs32& a, long long i,
 
 // Close averaging window w (counted from the clock reset) of V (Sec. IV) for
 // trajectory i.
-__device__ __forceinline__ void close_window32(const RunArgs32& a, long long i, const Traj32& t, long long w) {
+template <typename T>   // Traj32 or TrajDF: angle pairs and laps
+__device__ __forceinline__ void close_window32(const RunArgs32& a, long long i, const T& t, long long w) {
   const long long n = a.n;
   const double inv_dt = 1.0 / ((double)a.W * a.h);
   const double u = (double)t.u.hi + (double)t.u.lo, v = (double)t.v.hi + (double)t.v.lo,

@@ -83,7 +83,11 @@ __device__ __forceinline__ void init_common(const InitArgs& a, long long i, doub
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
       if (a.s.tg) a.s.tg[c * n + i] = t6[c];
-      if (a.f.tg) a.f.tg[c * n + i] = __double2float_rn(t6[c]);
+      if (a.f.tg) {
+        const float hi = __double2float_rn(t6[c]);
+        a.f.tg[c * n + i] = hi;
+        if (a.f.tg_lo) a.f.tg_lo[c * n + i] = __double2float_rn(t6[c] - (double)hi);
+      }
     }
   }
 }
@@ -216,7 +220,8 @@ __global__ void k_indicator(ReadArgs a) {
       }
       case ARNOLD_IND_TANGENT: {
         double w[6];
-        for (int c = 0; c < 6; ++c) w[c] = a.fp32c ? (double)a.f.tg[c * n + i] : a.s.tg[c * n + i];
+        for (int c = 0; c < 6; ++c)
+          w[c] = a.fp32c ? (double)a.f.tg[c * n + i] + (a.f.tg_lo ? (double)a.f.tg_lo[c * n + i] : 0.0) : a.s.tg[c * n + i];
         out[i] = 0.5 * (w[0] + w[1]);
         out[n + i] = 0.5 * (w[0] - w[1]);
         out[2 * n + i] = w[2];
@@ -252,7 +257,8 @@ __global__ void k_indicator(ReadArgs a) {
       case ARNOLD_IND_CHI:
       case ARNOLD_IND_CLASS: {
         double w[6];
-        for (int c = 0; c < 6; ++c) w[c] = a.fp32c ? (double)a.f.tg[c * n + i] : a.s.tg[c * n + i];
+        for (int c = 0; c < 6; ++c)
+          w[c] = a.fp32c ? (double)a.f.tg[c * n + i] + (a.f.tg_lo ? (double)a.f.tg_lo[c * n + i] : 0.0) : a.s.tg[c * n + i];
         const double n2 = 0.5 * (w[0] * w[0] + w[1] * w[1]) + w[2] * w[2] + 0.5 * (w[3] * w[3] + w[4] * w[4]) +
                           w[5] * w[5];
         const double chi = (a.s.logsum[i] + 0.5 * log(n2)) / a.t;

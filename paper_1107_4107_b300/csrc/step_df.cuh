@@ -126,12 +126,41 @@ __device__ __forceinline__ void sincos_df(const Pair& x, const float4* __restric
   }
 }
 
+// State of one DF64 trajectory: phase-space state and tangent as float pairs
+// (~48 bits each), laps as integers.
+struct TrajDF {
+  Pair u, v, z, qu, qv, pz;
+  Pair du, dv, dz, dqu, dqv, dpz;
+  int lu, lv, lz;
+};
+
+__device__ __forceinline__ Pair df_neg(const Pair& a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ Pair df_scale2(const Pair& a, float m) { return {m * a.hi, m * a.lo}; }   // m = +-2: exact
+
+// Drift in double-float: the state as in the FP32C path (TwoSum, s a float
+// pair), the tangent dX += s dP as double-float products accumulated with
+// TwoSum.
+template <bool TAN>
+__device__ __forceinline__ void drift_df(TrajDF& t, float sh, float sl) {
+  drift_comp<false>(t.u, sh, sl, t.qu);
+  drift_comp<false>(t.v, sh, sl, t.qv);
+  drift_comp<false>(t.z, sh, sl, t.pz);
+  if (TAN) {
+    const Pair s = {sh, sl};
+    df_acc(t.du, df_mul_u(s, t.dqu));
+    df_acc(t.dv, df_mul_u(s, t.dqv));
+    df_acc(t.dz, df_mul_u(s, t.dpz));
+  }
+}
+
 // Kick in double-float: q_u += G s_u, q_v += G s_v, p_z += Sp A with
 // G = (k2 c_z) c_z, Sp = (k2 c_z) s_z, A = c_u + c_v (k2 = 2 tau eps as a
-// pair); the tangent update uses the leading words in FP32 (as in the FP32C
-// path), its 4 tau eps c_z^2 as 2G.
+// pair).  The tangent update (the Hessian of Eq. 2 applied to the tangent) is
+// double-float as well, coefficients and accumulation: on a regular orbit the
+// tangent map is a shear, and FP32 coefficients or FP32 accumulation bias its
+// growth over 1e6 steps (the chi field then drifts by percents).
 template <bool TAN>
-__device__ __forceinline__ void kick_df(Traj32& t, const Pair& k2, const float4* tab, const TabDF& tb) {
+__device__ __forceinline__ void kick_df(TrajDF& t, const Pair& k2, const float4* tab, const TabDF& tb) {
   Pair su, cu, sv, cv, sz, cz;
   sincos_df(t.u, tab, tb, su, cu);
   sincos_df(t.v, tab, tb, sv, cv);
@@ -144,23 +173,23 @@ __device__ __forceinline__ void kick_df(Traj32& t, const Pair& k2, const float4*
   df_acc(t.qv, df_mul_u(G, sv));
   df_acc(t.pz, df_mul_u(Sp, A));
   if (TAN) {
-    const float Gf = G.hi, Spf = Sp.hi, Af = A.hi, k2f = k2.hi;
-    const float Gu = Gf * cu.hi, Gv = Gf * cv.hi;
-    const float Yu = Spf * su.hi, Yv = Spf * sv.hi;
-    const float Z = Af * fmaf(2.0f, Gf, -k2f);   // A (k4 c_z^2 - k2), k4 = 2 k2
-    const float m2dz = -2.0f * t.dz;
-    t.dqu = fmaf(Gu, t.du, t.dqu);
-    t.dqu = fmaf(Yu, m2dz, t.dqu);
-    t.dqv = fmaf(Gv, t.dv, t.dqv);
-    t.dqv = fmaf(Yv, m2dz, t.dqv);
-    t.dpz = fmaf(Z, t.dz, t.dpz);
-    t.dpz = fmaf(-Yu, t.du, t.dpz);
-    t.dpz = fmaf(-Yv, t.dv, t.dpz);
+    const Pair Gu = df_mul_u(G, cu), Gv = df_mul_u(G, cv);
+    const Pair Yu = df_mul_u(Sp, su), Yv = df_mul_u(Sp, sv);
+    const Pair Z = df_mul_u(A, df_add(df_scale2(G, 2.0f), df_neg(k2)));   // A (k4 c_z^2 - k2), k4 = 2 k2
+    const Pair m2dz = df_scale2(t.dz, -2.0f);
+    df_acc(t.dqu, df_mul_u(Gu, t.du));
+    df_acc(t.dqu, df_mul_u(Yu, m2dz));
+    df_acc(t.dqv, df_mul_u(Gv, t.dv));
+    df_acc(t.dqv, df_mul_u(Yv, m2dz));
+    df_acc(t.dpz, df_mul_u(Z, t.dz));
+    df_acc(t.dpz, df_mul_u(df_neg(Yu), t.du));
+    df_acc(t.dpz, df_mul_u(df_neg(Yv), t.dv));
   }
 }
 
 // Potential (Eq. 2) in double-float, returned as FP64.
-__device__ __forceinline__ double potential_df(const Traj32& t, const float4* tab, const TabDF& tb) {
+template <typename T>
+__device__ __forceinline__ double potential_df(const T& t, const float4* tab, const TabDF& tb) {
   Pair su, cu, sv, cv, sz, cz;
   sincos_df(t.u, tab, tb, su, cu);
   sincos_df(t.v, tab, tb, sv, cv);
@@ -191,9 +220,14 @@ __device__ __forceinline__ void reduce_angle_df(Pair& x, int& lap, const TabDF& 
   lap += k;
 }
 
-__device__ __forceinline__ void end_step_df(Traj32& t, const TabDF& tb) {
+template <bool TAN>
+__device__ __forceinline__ void end_step_df(TrajDF& t, const TabDF& tb) {
   renorm(t.qu); renorm(t.qv); renorm(t.pz);
   renorm(t.u); renorm(t.v); renorm(t.z);
+  if (TAN) {
+    renorm(t.du); renorm(t.dv); renorm(t.dz);
+    renorm(t.dqu); renorm(t.dqv); renorm(t.dpz);
+  }
   const int big = max(max(__float_as_int(t.u.hi) & 0x7FFFFFFF, __float_as_int(t.v.hi) & 0x7FFFFFFF),
                       __float_as_int(t.z.hi) & 0x7FFFFFFF);
   if (big > 0x41400000) {   // |angle| > 12
