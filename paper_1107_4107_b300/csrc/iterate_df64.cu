@@ -5,7 +5,9 @@
 // is evaluated in double-float (step_df.cuh): table sincos with the reduced
 // argument kept as a pair and the force products split exactly, so the map
 // is followed to ~1e-16 per operation like the FP64 kernel.  The tangent
-// vector stays in FP32 (its renormalisation logs in FP64).
+// vector is double-float too (pair components and coefficients, TwoSum
+// accumulation): on a regular orbit the tangent map is a shear whose growth
+// an FP32 tangent biases.  Its norm and log at renormalisation are FP64.
 #include "kernels.cuh"
 #include "run32.cuh"
 #include "step_df.cuh"
@@ -83,16 +85,15 @@ __global__ void __launch_bounds__(256) k_iterate_df64(IterArgs a, TabDF tb, Coef
           const double l = 0.5 * log(n2);
           logsum += l;
           if (a.s.megno) megno_update(a.s.megno, n, i, (a.step0 + s + 1) / a.R, l);
-          // rescale (the next log measures the norm actually left, so the
-          // rounding of the factor does not accumulate)
-          const float inv = rsqrtf(__double2float_rn(n2));
+          // rescale by 1/|w| to double-float accuracy: whatever norm the factor
+          // leaves enters the next log, so an FP32 factor (~1e-7) would add up
+          // over the renormalisations
+          const double inv = rsqrt(n2);
+          const float ih = __double2float_rn(inv);
+          const Pair iv = {ih, __double2float_rn(inv - (double)ih)};
           Pair* w[6] = {&t.du, &t.dv, &t.dz, &t.dqu, &t.dqv, &t.dpz};
 #pragma unroll
-          for (int c = 0; c < 6; ++c) {
-            const float p = __fmul_rn(w[c]->hi, inv);
-            const float e = fmaf(w[c]->lo, inv, fmaf(w[c]->hi, inv, -p));
-            fast_two_sum(p, e, w[c]->hi, w[c]->lo);
-          }
+          for (int c = 0; c < 6; ++c) *w[c] = df_mul(*w[c], iv);
           if (!(n2 > 0.0) || !isfinite(n2)) bad = 1;
         }
         const double kin = 0.25 * (pair_sq_d(t.qu) + pair_sq_d(t.qv)) + 0.5 * pair_sq_d(t.pz);

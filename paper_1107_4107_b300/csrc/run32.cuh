@@ -88,15 +88,16 @@ __device__ __forceinline__ void renorm_sample32(const RunArgs32& a, long long i,
                                                 double& demax, int& bad, const float2* ssc, const Tab32& tb,
                                                 long long j, bool own) {
   if (TAN) {
-    const float n2 = 0.5f * (t.du * t.du + t.dv * t.dv) + t.dz * t.dz + 0.5f * (t.dqu * t.dqu + t.dqv * t.dqv) +
-                     t.dpz * t.dpz;
-    const double l = 0.5 * (double)__logf(n2);
+    // norm and log in FP64 (once per R steps), rescale in FP32
+    const double du = t.du, dv = t.dv, dz = t.dz, dqu = t.dqu, dqv = t.dqv, dpz = t.dpz;
+    const double n2 = 0.5 * (du * du + dv * dv) + dz * dz + 0.5 * (dqu * dqu + dqv * dqv) + dpz * dpz;
+    const double l = 0.5 * log(n2);
     logsum += l;
     if (a.s.megno && own) megno_update(a.s.megno, a.n, i, j, l);
-    const float inv = rsqrtf(n2);
+    const float inv = rsqrtf(__double2float_rn(n2));
     t.du *= inv; t.dv *= inv; t.dz *= inv;
     t.dqu *= inv; t.dqv *= inv; t.dpz *= inv;
-    if (!(n2 > 0.0f) || !isfinite(n2)) bad |= 1;
+    if (!(n2 > 0.0) || !(n2 <= 3.4e38)) bad |= 1;   // NaN, zero, or beyond FP32 (the factor)
   }
   // angles move at most h |q| within a step (the drift weights' partial sums stay in
   // [0, 1]) and each drift adds at most 0.8 h |q|: with h |q| <= 400 they stay in
