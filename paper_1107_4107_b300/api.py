@@ -258,33 +258,60 @@ class ArnoldEnsemble:
               "arnold_debug_sincos")
 
 
+_MAP_FN = None
+
+
+def _map_function():
+    """The torch.autograd.Function of the N-step map, built on first use (importing
+    this module does not import torch)."""
+    global _MAP_FN
+    if _MAP_FN is None:
+        import torch
+
+        class ArnoldMap(torch.autograd.Function):
+            """(X0, P0, h, eps) -> (X_N unwrapped, P_N) on CUDA tensors [3][n]; the
+            backward pass is the CUDA adjoint (arnold_grad) over the sqrt(N)
+            checkpoints the forward pass stored.  h and eps may be floats or
+            0-d tensors; their gradients are returned as 0-d tensors."""
+
+            @staticmethod
+            def forward(ctx, X0, P0, h, eps, n_steps, ckpt_every, precision, scheme):
+                n = X0.shape[1]
+                ens = ArnoldEnsemble(n, eps=float(eps), h=float(h), scheme=scheme, precision=precision,
+                                     tangent=False, device=X0.device.index or 0)
+                ens.set_state(X0.detach().contiguous(), P0.detach().contiguous())
+                ens.forward_ckpt(n_steps, ckpt_every)
+                dX = torch.empty_like(X0)
+                PN = torch.empty_like(P0)
+                ens.indicator("dX", out=dX)
+                ens.indicator("P", out=PN)
+                ctx.ens = ens
+                return X0.detach() + dX, PN
+
+            @staticmethod
+            def backward(ctx, gX, gP):
+                ens = ctx.ens
+                gx0, gp0, gh, ge = ens.grad(gX.contiguous(), gP.contiguous())
+                ens.close()   # the checkpoints are spent: one backward per forward
+                ctx.ens = None
+                dev = gX.device
+                return gx0, gp0, gh.to(dev).reshape(()), ge.to(dev).reshape(()), None, None, None, None
+
+        _MAP_FN = ArnoldMap
+    return _MAP_FN
+
+
+def __getattr__(name):
+    if name == "ArnoldMap":
+        return _map_function()
+    raise AttributeError(f"module {__name__!r} has no attribute {name!r}")
+
+
 def arnold_map(X0, P0, h, eps, n_steps: int, ckpt_every: int = 0, precision: str = "fp64", scheme: str = "yoshida6a"):
     """Differentiable N-step map (X0, P0, h, eps) -> (X_N unwrapped, P_N) on torch CUDA
-    tensors; backward runs the CUDA adjoint with sqrt(N) checkpointing."""
-    import torch
-
-    class _ArnoldMap(torch.autograd.Function):
-        @staticmethod
-        def forward(ctx, X0, P0, h, eps):
-            n = X0.shape[1]
-            ens = ArnoldEnsemble(n, eps=float(eps), h=float(h), scheme=scheme, precision=precision, tangent=False,
-                                 device=X0.device.index or 0)
-            ens.set_state(X0.detach().contiguous(), P0.detach().contiguous())
-            ens.forward_ckpt(n_steps, ckpt_every)
-            dX = torch.empty_like(X0)
-            PN = torch.empty_like(P0)
-            ens.indicator("dX", out=dX)
-            ens.indicator("P", out=PN)
-            ctx.ens = ens
-            return X0.detach() + dX, PN
-
-        @staticmethod
-        def backward(ctx, gX, gP):
-            gx0, gp0, gh, ge = ctx.ens.grad(gX.contiguous(), gP.contiguous())
-            dev = gX.device
-            return gx0, gp0, gh.to(dev).reshape(()), ge.to(dev).reshape(())
-
-    return _ArnoldMap.apply(X0, P0, h, eps)
+    tensors (ArnoldMap.apply); backward runs the CUDA adjoint with sqrt(N)
+    checkpointing (ckpt_every = 0: sqrt(N))."""
+    return _map_function().apply(X0, P0, h, eps, int(n_steps), int(ckpt_every), precision, scheme)
 
 
 class ArnoldBatch:

@@ -181,3 +181,15 @@ def test_sharded_loss_merge_any_split():
         np.testing.assert_allclose(c["mean"], whole["mean"], rtol=1e-14)
         np.testing.assert_allclose(c["var"], whole["var"], rtol=1e-12)
         assert abs(c["loss"] - oracle.loss_variance(P)) <= 1e-12 * abs(c["loss"])
+
+
+def test_arnold_map_is_one_autograd_function():
+    """ArnoldMap is a single module-level torch.autograd.Function (built once, on
+    first use) and arnold_map applies it."""
+    torch = pytest.importorskip("torch")
+    from paper_1107_4107_b300 import api
+    F = api.ArnoldMap
+    assert issubclass(F, torch.autograd.Function)
+    assert api.ArnoldMap is F
+    with pytest.raises(AttributeError):
+        api.NoSuchName  # noqa: B018
