@@ -328,6 +328,7 @@ def main():
 
     adjoint = None if args.no_extras else adjoint_leg(stream, local, barrier)
     batch = None if args.no_extras else batch_leg(stream, local, barrier, args)
+    energies = None if args.no_extras else energies_leg(n, rank, local, stream, barrier, args.chunk)
 
     if rank != 0:
         if dist:
@@ -339,7 +340,7 @@ def main():
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(args),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(gpu_launches),
             "clocks": clk.summary(), "fp32c": fp32c, "df64": df64, "adjoint": adjoint, "batch": batch,
-            "probe": {"dfma_per_s": dfma, "ffma_per_s": ffma}}
+            "energies": energies, "probe": {"dfma_per_s": dfma, "ffma_per_s": ffma}}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -391,6 +392,39 @@ def precision_leg(prec, n, rank, device, stream, barrier, steps, chi64, cls64, f
     e.close()
     if prec == "fp32c":
         out["reduce64"] = reduce64_variant(n, rank, device, stream, barrier, steps, chi64, cls64)
+    return out
+
+
+def energies_leg(n, rank, device, stream, barrier, chunk):
+    """The 2048 x 2048 scan at the other energies of the FP64 config: E = 40 (the
+    10x moderate coupling, eps_eff = 0.05) and E = 15 (the paper's moderate
+    value, 2/15).  FP64 and FP32C from the same grid ICs, two chunks each (the
+    first untimed): rates, and FP32C's agreement with FP64 at that horizon."""
+    import torch
+    from paper_1107_4107_b300.api import ArnoldEnsemble
+    out = {}
+    for E_ in (40.0, 15.0):
+        row = {"eps_eff": 2.0 / E_}
+        res = {}
+        for prec in ("fp64", "fp32c"):
+            e = ArnoldEnsemble(n, precision=prec, device=device, stream=stream.cuda_stream)
+            e.init_grid(G, E_, seed=rank)
+            e.iterate(chunk)
+            barrier()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            e.iterate(chunk)
+            b.record(stream)
+            barrier()
+            row[prec] = n * chunk / (a.elapsed_time(b) * 1e-3)
+            res[prec] = (e.indicator("chi"), e.indicator("class"))
+            e.close()
+        row["steps"] = 2 * chunk
+        row["fp32c_class_agreement_vs_fp64"] = float(np.mean(res["fp32c"][1] == res["fp64"][1]))
+        row["fp32c_hist_l1_vs_fp64"] = hist_l1(res["fp32c"][0], res["fp64"][0])
+        out[f"E{E_:g}"] = row
+    out["unit"] = "map-steps/s"
     return out
 
 
