@@ -55,6 +55,12 @@ FP32C_ISSUED_PER_STEP_NCU = 961
 # Measured by ncu for k_iterate_fp64<7,true> (all pipes: FP64, FP32, INT, LSU):
 # profiles/k_iterate_fp64__grid2048_E400_1M_traj_20_steps.md
 FP64_ISSUED_PER_STEP_NCU = 8018
+# Nominal ALU peaks of the part from its published figures and unit counts:
+# FP64 1.25 TFLOP/s (at the 2032 MHz maximum SM clock) = 6.25e11 FP64 FMA
+# instructions/s; FP32 148 SMs x 128 lanes x 2032 MHz = 3.85e13 FFMA/s (also
+# the issue peak: one warp instruction per clock per SM sub-partition).
+NOMINAL_FP64_INSTR_PER_S = 1.25e12 / 2
+NOMINAL_FP32_INSTR_PER_S = 148 * 128 * 2032e6
 
 
 def parse():
@@ -275,14 +281,17 @@ def main():
     # of the dominant kernel (source count x map steps / CUDA-event launch time),
     # peak = the live DFMA probe (one FP64 instruction per lane-slot).
     roofline = {"bound": "alu", "kernel": "k_iterate_fp64<7,true>",
-                "achieved": pipe_instr / 1e12, "peak": dfma / 1e12, "unit": "T FP64-instr/s",
-                "frac": pipe_instr / dfma, "traffic": traffic_for("k_iterate_fp64"),
-                "peak_source": "measured live: DFMA probe (arnold_probe_peak)",
+                "achieved": pipe_instr / 1e12, "peak": NOMINAL_FP64_INSTR_PER_S / 1e12, "unit": "T FP64-instr/s",
+                "frac": pipe_instr / NOMINAL_FP64_INSTR_PER_S, "traffic": traffic_for("k_iterate_fp64"),
+                "peak_source": "nominal: 1.25 TFLOP/s FP64 (148 SMs at 2032 MHz) / 2 FLOP per FMA",
+                "probe_peak": dfma / 1e12, "frac_of_probe": pipe_instr / dfma,
+                "probe_source": "measured live: DFMA probe (arnold_probe_peak), %.2f of the nominal"
+                                % (dfma / NOMINAL_FP64_INSTR_PER_S),
                 "fp64_instr_per_map_step": FP64_INSTR_PER_STEP,
                 "fp64_tflops": achieved_flops / 1e12, "flop_per_map_step": FP64_FLOP_PER_STEP,
                 "issued_instr_per_map_step_ncu": FP64_ISSUED_PER_STEP_NCU,
-                "issue_frac": (map_steps_per_launch / (per_launch_ms * 1e-3) * FP64_ISSUED_PER_STEP_NCU / ffma
-                               if FP64_ISSUED_PER_STEP_NCU else None)}
+                "issue_frac": (map_steps_per_launch / (per_launch_ms * 1e-3) * FP64_ISSUED_PER_STEP_NCU
+                               / NOMINAL_FP32_INSTR_PER_S if FP64_ISSUED_PER_STEP_NCU else None)}
     tr = roofline["traffic"]
     roofline["dram_gbs"] = tr / (per_launch_ms * 1e-3) / 1e9 if tr else None   # measured bytes / launch time
 
@@ -384,11 +393,13 @@ def precision_leg(prec, n, rank, device, stream, barrier, steps, chi64, cls64, f
                              "tested in tests/test_gpu_fp32c.py)"}
     if instr is not None:
         out["roofline"] = {"bound": "alu", "kernel": "k_iterate_fp32c<7,true,false>",
-                           "achieved_instr_per_s": v * instr, "peak_instr_per_s": ffma, "frac": v * instr / ffma,
-                           "issue_frac": v * issued / ffma,
-                           "peak_source": "measured live: FFMA probe (1 warp instruction / clock / SMSP = the "
-                                          "issue peak)", "instr_per_map_step": instr,
-                           "issued_instr_per_map_step_ncu": issued}
+                           "achieved_instr_per_s": v * instr, "peak_instr_per_s": NOMINAL_FP32_INSTR_PER_S,
+                           "frac": v * instr / NOMINAL_FP32_INSTR_PER_S,
+                           "issue_frac": v * issued / NOMINAL_FP32_INSTR_PER_S,
+                           "peak_source": "nominal: 148 SMs x 128 FP32 lanes x 2032 MHz (= the issue peak, one "
+                                          "warp instruction / clock / SMSP)",
+                           "probe_peak_instr_per_s": ffma, "issue_frac_of_probe": v * issued / ffma,
+                           "instr_per_map_step": instr, "issued_instr_per_map_step_ncu": issued}
     e.close()
     if prec == "fp32c":
         out["reduce64"] = reduce64_variant(n, rank, device, stream, barrier, steps, chi64, cls64)
