@@ -547,8 +547,51 @@ def batch_leg(stream, device, barrier, args):
            "kernel_launches_per_run": b.launches - l0,
            "config": "64 (K, eps_eff) pairs, eps_eff log-grid [1e-5, 1e-1], K log-grid [(0.005T)^2, (0.02T)^2], "
                      "sizes log-U[1e3, 1e6], steps log-U[1e4, 1e6] x 0.01, FP32C"}
+    out["fp64_same_sets"] = batch_vs_fp64(b, sets, tuning, out["value"], stream, device, barrier)
     b.close()
     return out
+
+
+def batch_vs_fp64(b, sets, tuning, batch_rate, stream, device, barrier):
+    """The same sets as plain FP64 single ensembles, one launch sequence after
+    another (the way an FP64 code would run them): their rate, and the agreement
+    of the batched FP32C indicator field with FP64 over all sets' trajectories
+    (classes, and the L1 distance of the pooled log10 chi histograms)."""
+    import torch
+    from paper_1107_4107_b300.api import ArnoldEnsemble
+    b.init()
+    b.run()
+    b.sync()
+    R = tuning["renorm_every"]
+    bins = dict(bins=200, range=(-8, 1))
+    h64 = np.zeros(200)
+    h32 = np.zeros(200)
+    agree = total = steps = 0
+    ms = 0.0
+    for k, q in enumerate(sets):
+        e = ArnoldEnsemble(q["G"] ** 2, eps=q["eps"], h=q["h"], precision="fp64", renorm_every=R, device=device,
+                           stream=stream.cuda_stream)
+        e.init_grid(q["G"], q["E"], seed=q["seed"])
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        z = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e.iterate(q["n_steps"])
+        z.record(stream)
+        barrier()
+        ms += a.elapsed_time(z)
+        steps += q["G"] ** 2 * q["n_steps"]
+        c64, x64 = e.indicator("class"), e.indicator("chi")
+        c32, x32 = b.indicator(k, "class"), b.indicator(k, "chi")
+        agree += int(np.sum(c64 == c32))
+        total += c64.size
+        h64 += np.histogram(np.log10(np.clip(x64, 1e-300, None)), **bins)[0]
+        h32 += np.histogram(np.log10(np.clip(x32, 1e-300, None)), **bins)[0]
+        e.close()
+    rate = steps / (ms * 1e-3)
+    return {"value": rate, "unit": "map-steps/s", "seconds": ms * 1e-3, "batch_speedup": batch_rate / rate,
+            "class_agreement": agree / total, "hist_l1": float(np.abs(h32 / total - h64 / total).sum()),
+            "trajectories": total}
 
 
 def traffic_for(kernel: str):
