@@ -81,7 +81,7 @@ def test_df64_long_horizon_low_growth_cells():
     assert np.array_equal(e.indicator("class")[low], st.classify()[low])
 
 
-@pytest.mark.parametrize("E", [400.0, 40.0])
+@pytest.mark.parametrize("E", [400.0, 40.0, 15.0])
 def test_df64_grid_parity(E):
     G = 32
     st = oracle_grid_state(G, E, oracle_params())
@@ -127,7 +127,7 @@ def test_df64_resume_bitwise_and_no_adjoint():
 
 def test_df64_full_size_grid_sampled_cells():
     """The 2048 x 2048 scan in double-float (default launch configuration): 256 sampled
-    cells against the FP64 oracle one by one, 100 steps."""
+    cells against the FP64 oracle one by one, 100 steps (state, tangent, FTLE)."""
     G, E = 2048, 400.0
     e = _ens(G * G)
     e.init_grid(G, E)
@@ -136,3 +136,5 @@ def test_df64_full_size_grid_sampled_cells():
     st = oracle_grid_state(G, E, oracle_params(), cells=cells).advance(100, threads=4)
     assert rel_err(e.indicator("dX")[:, cells], st.unwrapped_displacement()) < TOL
     assert rel_err(e.indicator("P")[:, cells], st.P) < TOL
+    assert rel_err(e.indicator("tangent")[:, cells], st.W) < TOL
+    assert rel_err(e.indicator("chi")[cells], st.chi()) < TOL

@@ -105,7 +105,7 @@ def test_other_schemes_parity(torch_cuda, scheme):
     assert all(v < TOL for k, v in errs.items() if k not in ("X", "dE_max")), errs
 
 
-@pytest.mark.parametrize("E", [400.0, 40.0])
+@pytest.mark.parametrize("E", [400.0, 40.0, 15.0])
 def test_grid_parity_all_cells(torch_cuda, E):
     """A 32 x 32 grid (several blocks, ragged last block): every cell to 100 steps,
     each side from its own fixed-energy grid ICs (they differ by ~1 ulp in p_z)."""
@@ -290,3 +290,36 @@ def test_oracle_scale_scan_128x128_1e4_steps(torch_cuda, E):
     assert agree >= 0.995
     assert l1 <= 1e-2
     assert dlog < 1e-6
+
+
+def test_oracle_scale_scan_paper_moderate_E15(torch_cuda):
+    """The paper's moderate coupling, E = 15 (eps_eff = 2/15; reported beside the
+    configured E = 400 and 40).  A few per cent of the 128 x 128 cells are chaotic,
+    and over 1e4 steps the finite-time exponents of weakly chaotic cells straddle
+    the threshold, so two FP64 runs that differ by a single rounding already
+    disagree on some classes.  The bar is that intrinsic level, measured on the
+    oracle itself (its run from angles moved by one ulp): the GPU must agree with
+    the oracle to within 0.5 % of the oracle's agreement with itself, and its
+    chi-histogram L1 stay within max(1e-2, 2 x the oracle's own)."""
+    import os
+    G, E, S = 128, 15.0, 10000
+    threads = max(1, os.cpu_count() or 1)
+    ens = _ens(G * G)
+    ens.init_grid(G, E)
+    ens.iterate(S)
+    prm = oracle_params()
+    st = oracle_grid_state(G, E, prm).advance(S, threads=threads)
+    X, Pxy = inputs.grid_slice(G, E, prm.eps, seed=0)
+    P = np.zeros((3, G * G))
+    P[:2] = Pxy
+    P = oracle.pz_from_energy(E, prm.eps, X, P)
+    st2 = oracle.State(np.nextafter(X, np.inf), P, prm).advance(S, threads=threads)
+    ref_cls, ref_chi = st.classify(), st.chi()
+    a_gpu = float(np.mean(ens.indicator("class") == ref_cls))
+    a_own = float(np.mean(st2.classify() == ref_cls))
+    l1_gpu = _hist_l1(ens.indicator("chi"), ref_chi)
+    l1_own = _hist_l1(st2.chi(), ref_chi)
+    print(f"E=15: GPU vs oracle agreement {a_gpu:.5f}, L1 {l1_gpu:.2e}; oracle vs its one-ulp run "
+          f"{a_own:.5f}, L1 {l1_own:.2e}; chaotic {ref_cls.mean():.4f}")
+    assert a_gpu >= a_own - 0.005
+    assert l1_gpu <= max(1e-2, 2.0 * l1_own)
