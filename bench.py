@@ -526,7 +526,7 @@ def batch_leg(stream, device, barrier, args):
     from paper_1107_4107_b300.api import ArnoldBatch
     sets = params.batch_sets(step_scale=0.01)
     t0 = time.perf_counter()
-    tuning = tune.tune_batch(sets)
+    tuning = tune.tune_batch(sets, device=device)
     tune_s = time.perf_counter() - t0
     b = ArnoldBatch(sets, tuning=tuning, device=device, stream=stream.cuda_stream)
     b.init()

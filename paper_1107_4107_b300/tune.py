@@ -19,9 +19,9 @@ CANDIDATES = [{"block_size": b, "traj_per_thread": t, "renorm_every": r, "epoch_
               for b in (128, 256) for t in (1, 2) for r in (50, 100, 200)]
 
 
-def _key(scheme: str, tangent: bool) -> str:
+def _key(scheme: str, tangent: bool, device: int) -> str:
     import torch
-    return f"{torch.cuda.get_device_name()}|fp32c|{scheme}|{int(tangent)}"
+    return f"{torch.cuda.get_device_name(device)}|fp32c|{scheme}|{int(tangent)}"
 
 
 def scaled(sets, g_div: int = 4, step_div: int = 200):
@@ -29,10 +29,13 @@ def scaled(sets, g_div: int = 4, step_div: int = 200):
 
 
 def tune_batch(sets, scheme: str = "yoshida6a", tangent: bool = True, use_cache: bool = True,
-               candidates=None, verbose: bool = False) -> dict:
+               candidates=None, verbose: bool = False, device: int | None = None) -> dict:
+    """Best tuning for `sets` on `device` (default: torch's current device)."""
     import torch
     from .api import ArnoldBatch
-    key = _key(scheme, tangent)
+    if device is None:
+        device = torch.cuda.current_device()
+    key = _key(scheme, tangent, device)
     cache = {}
     if use_cache and os.path.exists(CACHE):
         try:
@@ -43,9 +46,10 @@ def tune_batch(sets, scheme: str = "yoshida6a", tangent: bool = True, use_cache:
             return cache[key]["tuning"]
     sample = scaled(sets)
     results = []
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.current_stream(device)
     for cand in candidates or CANDIDATES:
-        b = ArnoldBatch(sample, scheme=scheme, tangent=tangent, tuning=cand)
+        b = ArnoldBatch(sample, scheme=scheme, tangent=tangent, tuning=cand, device=device,
+                        stream=stream.cuda_stream)
         b.init()
         b.run()          # captures the graph, warms up
         b.sync()
@@ -65,5 +69,10 @@ def tune_batch(sets, scheme: str = "yoshida6a", tangent: bool = True, use_cache:
     cache[key] = {"tuning": best[1], "rate_sample": best[0],
                   "all": [{"tuning": c, "rate": r} for r, c in results]}
     if use_cache:
-        json.dump(cache, open(CACHE, "w"), indent=1)
+        # several processes (one per GPU) may tune at once: write a private file
+        # and rename it over the cache, so a reader never sees a partial file
+        tmp = f"{CACHE}.{os.getpid()}.tmp"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1)
+        os.replace(tmp, CACHE)
     return best[1]
