@@ -1,6 +1,7 @@
 """A small, fixed case of the hot path for profilers (ncu) and quick timing.
 
     python -m paper_1107_4107_b300.profile_case --precision fp64 --n 1048576 --steps 20 --launches 3
+    python -m paper_1107_4107_b300.profile_case --batch 0.01 --launches 2
 
 Grid-slice ICs at E = 400 (the scan's initial conditions on a sqrt(n)-wide
 band of the 2048-wide grid), then `launches` calls of iterate(steps), each one
@@ -22,9 +23,32 @@ def main():
     ap.add_argument("--adjoint", type=int, default=0, metavar="C",
                     help="instead: the FP64/FP32C adjoint of the variance loss over --steps steps of --n box "
                          "trajectories with checkpoints every C steps (one k_adjoint launch per segment)")
+    ap.add_argument("--batch", type=float, default=0.0, metavar="SCALE",
+                    help="instead: the 64-set batch (FP32C) with steps scaled by SCALE and a fixed tuning "
+                         "(block 128, 1 trajectory per thread, R 200, 200 ms epochs): --launches graph runs")
     a = ap.parse_args()
     import torch
     from .api import ArnoldEnsemble
+    if a.batch:
+        from . import params
+        from .api import ArnoldBatch
+        b = ArnoldBatch(params.batch_sets(step_scale=a.batch),
+                        tuning={"block_size": 128, "traj_per_thread": 1, "renorm_every": 200, "epoch_ms": 200},
+                        stream=torch.cuda.current_stream().cuda_stream)
+        times = []
+        for _ in range(a.launches):
+            b.init()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            b.run()
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        b.sync()
+        info = b.info()
+        print(json.dumps({"batch": a.batch, "ms": times, "epochs": info["epochs"], "items": info["items"],
+                          "map_steps_per_s": info["map_steps_per_run"] / (min(times) * 1e-3)}))
+        return
     if a.adjoint:
         from . import inputs
         X, P = inputs.box(a.n, seed=0)
