@@ -172,100 +172,158 @@ __device__ __forceinline__ double load_pair(const Fp32cState& f, long long k) {
   return (double)f.hi[k] + (double)f.lo[k];
 }
 
-__global__ void k_indicator(ReadArgs a) {
+// The indicator of one trajectory: `v` holds its value in each output row
+// (3 for X, P, dX, V; 6 for the tangent; 1 otherwise), `b` the byte of the
+// u8 kinds.  Only the arrays the kind needs are read.
+__device__ __forceinline__ void indicator_one(const ReadArgs& a, long long i, double* v, unsigned char& b) {
   const long long n = a.n;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    double u, v, z, qu, qv, pz;
+  double u = 0.0, vv = 0.0, z = 0.0, qu = 0.0, qv = 0.0, pz = 0.0;
+  int lu = 0, lv = 0, lz = 0;
+  auto load_state = [&]() {
     if (a.fp32c) {
-      u = load_pair(a.f, i); v = load_pair(a.f, n + i); z = load_pair(a.f, 2 * n + i);
+      u = load_pair(a.f, i); vv = load_pair(a.f, n + i); z = load_pair(a.f, 2 * n + i);
       qu = load_pair(a.f, 3 * n + i); qv = load_pair(a.f, 4 * n + i); pz = load_pair(a.f, 5 * n + i);
     } else {
-      u = a.s.st[i]; v = a.s.st[n + i]; z = a.s.st[2 * n + i];
+      u = a.s.st[i]; vv = a.s.st[n + i]; z = a.s.st[2 * n + i];
       qu = a.s.st[3 * n + i]; qv = a.s.st[4 * n + i]; pz = a.s.st[5 * n + i];
     }
-    int lu = a.s.lap[i], lv = a.s.lap[n + i], lz = a.s.lap[2 * n + i];
+    lu = a.s.lap[i]; lv = a.s.lap[n + i]; lz = a.s.lap[2 * n + i];
     if (a.fp32c) {   // pair states keep angles unreduced between exact reductions: bring them into [0, 2pi)
       lu += reduce_any(u);
-      lv += reduce_any(v);
+      lv += reduce_any(vv);
       lz += reduce_any(z);
     }
-    double* out = (double*)a.out;
-    switch (a.kind) {
-      case ARNOLD_IND_X: {
-        const int par = (lu + lv) & 1;
-        out[i] = reduce_pi_parity(0.5 * (u + v), par);
-        out[n + i] = reduce_pi_parity(0.5 * (u - v), par);
-        out[2 * n + i] = z;
+  };
+  auto load_tangent = [&](double* w) {
+    for (int c = 0; c < 6; ++c)
+      w[c] = a.fp32c ? (double)a.f.tg[c * n + i] + (a.f.tg_lo ? (double)a.f.tg_lo[c * n + i] : 0.0)
+                     : a.s.tg[c * n + i];
+  };
+  switch (a.kind) {
+    case ARNOLD_IND_X: {
+      load_state();
+      const int par = (lu + lv) & 1;
+      v[0] = reduce_pi_parity(0.5 * (u + vv), par);
+      v[1] = reduce_pi_parity(0.5 * (u - vv), par);
+      v[2] = z;
+      break;
+    }
+    case ARNOLD_IND_P:
+      load_state();
+      v[0] = 0.5 * (qu + qv);
+      v[1] = 0.5 * (qu - qv);
+      v[2] = pz;
+      break;
+    case ARNOLD_IND_DX:
+    case ARNOLD_IND_V: {
+      if (a.kind == ARNOLD_IND_V && a.W > 0) {
+        v[0] = a.s.V[i]; v[1] = a.s.V[n + i]; v[2] = a.s.V[2 * n + i];
         break;
       }
-      case ARNOLD_IND_P:
-        out[i] = 0.5 * (qu + qv);
-        out[n + i] = 0.5 * (qu - qv);
-        out[2 * n + i] = pz;
-        break;
-      case ARNOLD_IND_DX:
-      case ARNOLD_IND_V: {
-        if (a.kind == ARNOLD_IND_V && a.W > 0) {
-          out[i] = a.s.V[i]; out[n + i] = a.s.V[n + i]; out[2 * n + i] = a.s.V[2 * n + i];
-          break;
-        }
-        const double dU = (u - a.s.ref[i]) + kTwoPi * (double)(lu - a.s.lapref[i]);
-        const double dV = (v - a.s.ref[n + i]) + kTwoPi * (double)(lv - a.s.lapref[n + i]);
-        const double dZ = (z - a.s.ref[2 * n + i]) + kTwoPi * (double)(lz - a.s.lapref[2 * n + i]);
-        const double sc = a.kind == ARNOLD_IND_V ? 1.0 / a.t : 1.0;
-        out[i] = 0.5 * (dU + dV) * sc;
-        out[n + i] = 0.5 * (dU - dV) * sc;
-        out[2 * n + i] = dZ * sc;
-        break;
-      }
-      case ARNOLD_IND_TANGENT: {
-        double w[6];
-        for (int c = 0; c < 6; ++c)
-          w[c] = a.fp32c ? (double)a.f.tg[c * n + i] + (a.f.tg_lo ? (double)a.f.tg_lo[c * n + i] : 0.0) : a.s.tg[c * n + i];
-        out[i] = 0.5 * (w[0] + w[1]);
-        out[n + i] = 0.5 * (w[0] - w[1]);
-        out[2 * n + i] = w[2];
-        out[3 * n + i] = 0.5 * (w[3] + w[4]);
-        out[4 * n + i] = 0.5 * (w[3] - w[4]);
-        out[5 * n + i] = w[5];
-        break;
-      }
-      case ARNOLD_IND_LOGSUM:
-        out[i] = a.s.logsum[i];
-        break;
-      case ARNOLD_IND_MEGNO:      // <Y>_m = Ysum / m (0 before the first renormalisation)
-        out[i] = a.m > 0 ? a.s.megno[n + i] / (double)a.m : 0.0;
-        break;
-      case ARNOLD_IND_MEGNO_Y:    // Y_m = 2 S / m
-        out[i] = a.m > 0 ? 2.0 * a.s.megno[i] / (double)a.m : 0.0;
-        break;
-      case ARNOLD_IND_LEFT:
-        ((unsigned char*)a.out)[i] = a.s.left ? a.s.left[i] : 0;
-        break;
-      case ARNOLD_IND_DE_MAX:
-        out[i] = a.s.demax[i];
-        break;
-      case ARNOLD_IND_DE: {
-        double su, cu, sv, cv, sz, cz;
-        sincos_tab64(u, a.sc, a.th, su, cu);
-        sincos_tab64(v, a.sc, a.th, sv, cv);
-        sincos_tab64(z, a.sc, a.th, sz, cz);
-        const double H = 0.25 * (qu * qu + qv * qv) + 0.5 * (pz * pz) + a.eps * ((cu + cv) * (cz * cz));
-        out[i] = fabs(H - a.s.e0[i]);
-        break;
-      }
-      case ARNOLD_IND_CHI:
-      case ARNOLD_IND_CLASS: {
-        double w[6];
-        for (int c = 0; c < 6; ++c)
-          w[c] = a.fp32c ? (double)a.f.tg[c * n + i] + (a.f.tg_lo ? (double)a.f.tg_lo[c * n + i] : 0.0) : a.s.tg[c * n + i];
-        const double n2 = 0.5 * (w[0] * w[0] + w[1] * w[1]) + w[2] * w[2] + 0.5 * (w[3] * w[3] + w[4] * w[4]) +
-                          w[5] * w[5];
-        const double chi = (a.s.logsum[i] + 0.5 * log(n2)) / a.t;
-        if (a.kind == ARNOLD_IND_CHI) out[i] = chi;
-        else ((unsigned char*)a.out)[i] = chi > a.threshold ? 1 : 0;
-        break;
-      }
+      load_state();
+      const double dU = (u - a.s.ref[i]) + kTwoPi * (double)(lu - a.s.lapref[i]);
+      const double dV = (vv - a.s.ref[n + i]) + kTwoPi * (double)(lv - a.s.lapref[n + i]);
+      const double dZ = (z - a.s.ref[2 * n + i]) + kTwoPi * (double)(lz - a.s.lapref[2 * n + i]);
+      const double sc = a.kind == ARNOLD_IND_V ? 1.0 / a.t : 1.0;
+      v[0] = 0.5 * (dU + dV) * sc;
+      v[1] = 0.5 * (dU - dV) * sc;
+      v[2] = dZ * sc;
+      break;
+    }
+    case ARNOLD_IND_TANGENT: {
+      double w[6];
+      load_tangent(w);
+      v[0] = 0.5 * (w[0] + w[1]);
+      v[1] = 0.5 * (w[0] - w[1]);
+      v[2] = w[2];
+      v[3] = 0.5 * (w[3] + w[4]);
+      v[4] = 0.5 * (w[3] - w[4]);
+      v[5] = w[5];
+      break;
+    }
+    case ARNOLD_IND_LOGSUM:
+      v[0] = a.s.logsum[i];
+      break;
+    case ARNOLD_IND_MEGNO:      // <Y>_m = Ysum / m (0 before the first renormalisation)
+      v[0] = a.m > 0 ? a.s.megno[n + i] / (double)a.m : 0.0;
+      break;
+    case ARNOLD_IND_MEGNO_Y:    // Y_m = 2 S / m
+      v[0] = a.m > 0 ? 2.0 * a.s.megno[i] / (double)a.m : 0.0;
+      break;
+    case ARNOLD_IND_LEFT:
+      b = a.s.left ? a.s.left[i] : 0;
+      break;
+    case ARNOLD_IND_DE_MAX:
+      v[0] = a.s.demax[i];
+      break;
+    case ARNOLD_IND_DE: {
+      load_state();
+      double su, cu, sv, cv, sz, cz;
+      sincos_tab64(u, a.sc, a.th, su, cu);
+      sincos_tab64(vv, a.sc, a.th, sv, cv);
+      sincos_tab64(z, a.sc, a.th, sz, cz);
+      const double H = 0.25 * (qu * qu + qv * qv) + 0.5 * (pz * pz) + a.eps * ((cu + cv) * (cz * cz));
+      v[0] = fabs(H - a.s.e0[i]);
+      break;
+    }
+    case ARNOLD_IND_CHI:
+    case ARNOLD_IND_CLASS: {
+      double w[6];
+      load_tangent(w);
+      const double n2 = 0.5 * (w[0] * w[0] + w[1] * w[1]) + w[2] * w[2] + 0.5 * (w[3] * w[3] + w[4] * w[4]) +
+                        w[5] * w[5];
+      const double chi = (a.s.logsum[i] + 0.5 * log(n2)) / a.t;
+      v[0] = chi;
+      b = chi > a.threshold ? 1 : 0;
+      break;
+    }
+  }
+}
+
+// Values of trajectories i and i + 1 in one SoA row: a 16-byte (or 2-byte)
+// vector store when both exist and the address is aligned (a row starts at
+// r n, so an odd n misaligns every other row), scalar stores otherwise.
+__device__ __forceinline__ void put2(double* row, long long i, bool two, double x0, double x1) {
+  double* p = row + i;
+  if (two && (reinterpret_cast<unsigned long long>(p) & 15ULL) == 0) {
+    *reinterpret_cast<double2*>(p) = make_double2(x0, x1);
+  } else {
+    p[0] = x0;
+    if (two) p[1] = x1;
+  }
+}
+__device__ __forceinline__ void put2(unsigned char* row, long long i, bool two, unsigned char x0,
+                                     unsigned char x1) {
+  unsigned char* p = row + i;
+  if (two && (reinterpret_cast<unsigned long long>(p) & 1ULL) == 0) {
+    *reinterpret_cast<uchar2*>(p) = make_uchar2(x0, x1);
+  } else {
+    p[0] = x0;
+    if (two) p[1] = x1;
+  }
+}
+
+// Read-out: each thread computes two consecutive trajectories and writes them
+// with vector stores, so a warp writes 512 contiguous bytes of every f64 row.
+__global__ void k_indicator(ReadArgs a) {
+  const long long n = a.n;
+  const int rows = (a.kind == ARNOLD_IND_TANGENT) ? 6
+                   : (a.kind == ARNOLD_IND_X || a.kind == ARNOLD_IND_P || a.kind == ARNOLD_IND_DX ||
+                      a.kind == ARNOLD_IND_V) ? 3 : 1;
+  const bool bytes = a.kind == ARNOLD_IND_CLASS || a.kind == ARNOLD_IND_LEFT;
+  for (long long i = 2 * ((long long)blockIdx.x * blockDim.x + threadIdx.x); i < n;
+       i += 2 * (long long)gridDim.x * blockDim.x) {
+    const bool two = i + 1 < n;
+    double v0[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, v1[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    unsigned char b0 = 0, b1 = 0;
+    indicator_one(a, i, v0, b0);
+    if (two) indicator_one(a, i + 1, v1, b1);
+    if (bytes) {
+      put2((unsigned char*)a.out, i, two, b0, b1);
+    } else {
+#pragma unroll
+      for (int r = 0; r < 6; ++r)
+        if (r < rows) put2((double*)a.out + r * n, i, two, v0[r], v1[r]);
     }
   }
 }

@@ -5,7 +5,8 @@
 // maximum energy error and Welford mean / second moment of each momentum
 // component.  Pass 1: every block reduces a grid-stride share of the
 // trajectories (shared-memory histogram; per-thread Welford accumulators
-// merged by a fixed binary tree) into one partial in the context's scratch.
+// merged by a fixed warp-shuffle tree, then across the block's warps) into one
+// partial in the context's scratch.
 // Pass 2: the partials are merged in block order, so the result is
 // deterministic.
 #include <math.h>
@@ -48,12 +49,32 @@ __device__ __forceinline__ void merge(Acc& a, const Acc& b) {
   a.over += b.over;
 }
 
+// Lane l merges lane l + o for o = 16, 8, 4, 2, 1 (a fixed tree, so the result
+// does not depend on timing); lane 0 ends with the warp's accumulator.
+__device__ __forceinline__ void warp_merge(Acc& a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    Acc b;
+    b.cnt = __shfl_down_sync(0xffffffffu, a.cnt, o);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      b.mean[c] = __shfl_down_sync(0xffffffffu, a.mean[c], o);
+      b.m2[c] = __shfl_down_sync(0xffffffffu, a.m2[c], o);
+    }
+    b.demax = __shfl_down_sync(0xffffffffu, a.demax, o);
+    b.chaotic = __shfl_down_sync(0xffffffffu, a.chaotic, o);
+    b.under = __shfl_down_sync(0xffffffffu, a.under, o);
+    b.over = __shfl_down_sync(0xffffffffu, a.over, o);
+    if ((threadIdx.x & 31) + o < 32) merge(a, b);
+  }
+}
+
 __global__ void __launch_bounds__(kStatsThreads) k_stats_partial(long long n, const double* __restrict__ chi,
                                                                  const double* __restrict__ dE,
                                                                  const double* __restrict__ p, double threshold,
                                                                  StatsPartial* __restrict__ partials) {
   __shared__ unsigned int hist[ARNOLD_HIST_BINS];
-  __shared__ Acc red[kStatsThreads];
+  __shared__ Acc red[kStatsThreads / 32];
   for (int k = threadIdx.x; k < ARNOLD_HIST_BINS; k += blockDim.x) hist[k] = 0;
   __syncthreads();
   Acc a;
@@ -80,12 +101,18 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats_partial(long long n, co
       a.m2[c] += d * (xv - a.mean[c]);
     }
   }
-  red[threadIdx.x] = a;
+  warp_merge(a);
+  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0) red[warp] = a;
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) merge(red[threadIdx.x], red[threadIdx.x + s]);
-    __syncthreads();
+  if (warp == 0) {   // the warps' accumulators, merged by the same tree
+    Acc w;
+    if (threadIdx.x < nwarps) w = red[threadIdx.x];
+    else acc_zero(w);
+    warp_merge(w);
+    if (threadIdx.x == 0) red[0] = w;
   }
+  __syncthreads();
   StatsPartial& out = partials[blockIdx.x];
   for (int k = threadIdx.x; k < ARNOLD_HIST_BINS; k += blockDim.x) out.hist[k] = hist[k];
   if (threadIdx.x == 0) {
