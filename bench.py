@@ -329,11 +329,14 @@ def main():
     cls64 = ens.indicator("class")
     fp32c = None
     df64 = None
+    df64f = None
     if not args.no_fp32c:
         fp32c = precision_leg("fp32c", n, rank, local, stream, barrier, fp64_steps, chi64, cls64, value / world,
                               ffma, FP32C_INSTR_PER_STEP, FP32C_ISSUED_PER_STEP_NCU)
         df64 = precision_leg("df64", n, rank, local, stream, barrier, fp64_steps, chi64, cls64, value / world,
                              ffma, None, None)
+        df64f = precision_leg("df64f", n, rank, local, stream, barrier, fp64_steps, chi64, cls64, value / world,
+                              ffma, None, None)
 
     adjoint = None if args.no_extras else adjoint_leg(stream, local, barrier)
     batch = None if args.no_extras else batch_leg(stream, local, barrier, args)
@@ -348,7 +351,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(args),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(gpu_launches),
-            "clocks": clk.summary(), "fp32c": fp32c, "df64": df64, "adjoint": adjoint, "batch": batch,
+            "clocks": clk.summary(), "fp32c": fp32c, "df64": df64, "df64f": df64f, "adjoint": adjoint, "batch": batch,
             "energies": energies, "probe": {"dfma_per_s": dfma, "ffma_per_s": ffma}}
     print(json.dumps(line), flush=True)
     if dist:

@@ -48,7 +48,7 @@ extern "C" {
 #define ARNOLD_ENONFINITE   -5  /* the state became NaN/Inf (checked when results are read)         */
 #define ARNOLD_EUNSUPPORTED -6  /* combination not built (e.g. no CUDA device)                      */
 #define ARNOLD_ESTATE       -7  /* call out of order (e.g. arnold_grad before arnold_forward_ckpt)  */
-#define ARNOLD_ERANGE       -8  /* outside the precision mode's range (h |q| per step > 9 for DF64, > 400 for FP32C) */
+#define ARNOLD_ERANGE       -8  /* outside the precision mode's range (h |q| per step > 9 for DF64 and DF64F, > 400 for FP32C) */
 
 /* ---- enums --------------------------------------------------------------- */
 /* Integrators (Sec. III names a sixth-order symplectic scheme whose reference
@@ -61,8 +61,11 @@ extern "C" {
                            Sec. III); FP64 instructions only where that accuracy needs them             */
 #define ARNOLD_FP32C 1  /* compensated FP32: float-pair angles (held in a [1024, 2048) rad window, whole
                            turns removed exactly) and momenta, two-sum updates; FP64 logs and energy     */
-#define ARNOLD_DF64  2  /* double-float: state and kicks in float pairs (~48-bit), FP64-grade trajectories
-                           on the FP32 pipes; tangent in FP32.  No adjoint or batch.                   */
+#define ARNOLD_DF64  2  /* double-float: state, kicks and tangent in float pairs (~48-bit), FP64-grade
+                           trajectories on the FP32 pipes.  No adjoint or batch.                        */
+#define ARNOLD_DF64F 3  /* DF64 with a faster sincos: the same double-float state, products, sums and
+                           tangent, but sines and cosines to ~3e-10 (FP32 reduced argument joined to the
+                           table's float pairs).  No adjoint or batch.                                   */
 
 #define ARNOLD_HOST   0
 #define ARNOLD_DEVICE 1
@@ -95,7 +98,7 @@ typedef struct arnold_params {
   double  eps;           /* eps of Eq. 1 (the paper uses 1, Eq. 3)                          */
   double  h;             /* composite step, != 0 (paper: 0.01 * 2 pi, Sec. III)             */
   int32_t scheme;        /* ARNOLD_SCHEME_*                                                 */
-  int32_t precision;     /* ARNOLD_FP64, ARNOLD_FP32C or ARNOLD_DF64                        */
+  int32_t precision;     /* ARNOLD_FP64, ARNOLD_FP32C, ARNOLD_DF64 or ARNOLD_DF64F          */
   int32_t tangent;       /* 1: carry the tangent vector and FTLE; 0: state only            */
   int32_t renorm_every;  /* R >= 1: tangent renormalisation / energy sampling interval      */
   int64_t window;        /* W >= 0: steps per averaging window of V; 0 = whole run          */
@@ -257,7 +260,9 @@ int arnold_stats_arrays_noalloc(int device, void* cuda_stream, int64_t n, const 
  * arnold_iterate, storing the state every ckpt_every steps (0: ceil(sqrt(n)))
  * in library-owned device memory (ceil(n_steps/C) + C states per trajectory).
  * Any later set_state / init_grid / iterate discards the checkpoints.
- * Errors: EINVAL, ENOMEM, ECUDA. */
+ * FP64 and FP32C contexts only (FP32C with the FP32 window reduction).
+ * Errors: EINVAL, ENOMEM, ECUDA, EUNSUPPORTED (DF64, DF64F, the FP32C
+ * FP64-reduction variant). */
 int arnold_forward_ckpt(arnold_ctx* ctx, int64_t n_steps, int64_t ckpt_every);
 
 /* arnold_grad: given dL/dX_N and dL/dP_N ([3][n] f64 each, in the paper's

@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(HERE, "libarnold.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, EUNSUPPORTED, ESTATE, ERANGE = 0, -1, -2, -3, -4, -5, -6, -7, -8
 SCHEMES = {"yoshida6a": 0, "triplejump6": 1, "leapfrog2": 2}
-PRECISIONS = {"fp64": 0, "fp32c": 1, "df64": 2}
+PRECISIONS = {"fp64": 0, "fp32c": 1, "df64": 2, "df64f": 3}
 HOST, DEVICE = 0, 1
 IND = {"chi": 0, "V": 1, "dE": 2, "dE_max": 3, "class": 4, "X": 5, "P": 6, "dX": 7, "tangent": 8, "logsum": 9,
        "left": 10, "megno": 11, "megno_y": 12}

@@ -131,7 +131,7 @@ int params_ok(const arnold_params* p) {
   if (!p) return 0;
   if (!(p->h != 0.0) || !isfinite(p->h) || !isfinite(p->eps)) return 0;
   if (p->scheme < 0 || p->scheme > 2) return 0;
-  if (p->precision != ARNOLD_FP64 && p->precision != ARNOLD_FP32C && p->precision != ARNOLD_DF64) return 0;
+  if (p->precision < ARNOLD_FP64 || p->precision > ARNOLD_DF64F) return 0;
   if (p->tangent != 0 && p->tangent != 1) return 0;
   if (p->renorm_every < 1 || p->window < 0) return 0;
   if (!(p->chaos_kappa > 0.0)) return 0;
@@ -411,7 +411,8 @@ int arnold_create(const arnold_params* prm, int64_t n_traj, int device, void* cu
     e = dalloc(&c->f.hi, 6 * n);
     if (e == cudaSuccess) e = dalloc(&c->f.lo, 6 * n);
     if (e == cudaSuccess && tan) e = dalloc(&c->f.tg, 6 * n);
-    if (e == cudaSuccess && tan && prm->precision == ARNOLD_DF64) e = dalloc(&c->f.tg_lo, 6 * n);
+    if (e == cudaSuccess && tan && (prm->precision == ARNOLD_DF64 || prm->precision == ARNOLD_DF64F))
+      e = dalloc(&c->f.tg_lo, 6 * n);
   }
   if (e == cudaSuccess) e = dalloc(&c->s.lap, 3 * n);
   if (e == cudaSuccess) e = dalloc(&c->s.lapref, 3 * n);
@@ -571,7 +572,8 @@ int arnold_iterate(arnold_ctx* c, int64_t n_steps) {
   ACHECK(cudaSetDevice(c->device));
   const arnold_params& p = c->prm;
   const bool fp32c = p.precision == ARNOLD_FP32C;
-  const bool df64 = p.precision == ARNOLD_DF64;
+  const bool df64 = p.precision == ARNOLD_DF64 || p.precision == ARNOLD_DF64F;
+  const bool fast = p.precision == ARNOLD_DF64F;
   int block = p.block_size;
   if (block == 0) {
     block = 256;
@@ -580,7 +582,7 @@ int arnold_iterate(arnold_ctx* c, int64_t n_steps) {
     if (block < 32) block = 32;
   }
   const int bps = fp32c  ? fp32c_blocks_per_sm(p.scheme, p.tangent, block)
-                  : df64 ? df64_blocks_per_sm(p.scheme, p.tangent, block)
+                  : df64 ? df64_blocks_per_sm(p.scheme, p.tangent, fast, block)
                          : fp64_blocks_per_sm(p.scheme, p.tangent, block);
   long long grid = (c->n + block - 1) / block;
   const long long cap = (long long)c->sms * bps;
@@ -588,7 +590,7 @@ int arnold_iterate(arnold_ctx* c, int64_t n_steps) {
   long long chunk = p.launch_steps;
   if (chunk == 0) {
     // aim at ~0.2 s per launch from the measured rates (map-steps/s, 7 kicks)
-    const double rate = (fp32c ? 3.0e10 : (df64 ? 8.0e9 : 1.0e9)) * 7.0 / (double)make_coef(p).m;
+    const double rate = (fp32c ? 3.0e10 : (fast ? 1.2e10 : (df64 ? 8.0e9 : 1.0e9))) * 7.0 / (double)make_coef(p).m;
     chunk = (long long)(0.2 * rate / (double)c->n);
     if (chunk < 1) chunk = 1;
     if (chunk > (1 << 20)) chunk = 1 << 20;
@@ -614,7 +616,7 @@ int arnold_iterate(arnold_ctx* c, int64_t n_steps) {
     a.step0 = c->steps;
     a.nsteps = (int)s;
     cudaError_t e = fp32c  ? launch_iterate_fp32c_v(a, p.scheme, p.tangent, c->reduce64, block, (int)grid, c->stream)
-                    : df64 ? launch_iterate_df64(a, p.scheme, p.tangent, block, (int)grid, c->stream)
+                    : df64 ? launch_iterate_df64(a, p.scheme, p.tangent, fast, block, (int)grid, c->stream)
                            : launch_iterate_fp64(a, p.scheme, p.tangent, block, (int)grid, c->stream);
     if (e != cudaSuccess) return cuda_status(e);
     c->launches++;
@@ -717,7 +719,9 @@ static int ensure_bytes(void** p, size_t* have, size_t need) {
 
 int arnold_forward_ckpt(arnold_ctx* c, int64_t n_steps, int64_t ckpt_every) {
   if (!c || n_steps < 1 || ckpt_every < 0) return ARNOLD_EINVAL;
-  if ((c->prm.precision == ARNOLD_FP32C && c->reduce64) || c->prm.precision == ARNOLD_DF64) return ARNOLD_EUNSUPPORTED;
+  if ((c->prm.precision == ARNOLD_FP32C && c->reduce64) || c->prm.precision == ARNOLD_DF64 ||
+      c->prm.precision == ARNOLD_DF64F)
+    return ARNOLD_EUNSUPPORTED;
   ACHECK(cudaSetDevice(c->device));
   long long C = ckpt_every > 0 ? ckpt_every : (long long)ceil(sqrt((double)n_steps));
   if (C > n_steps) C = n_steps;
@@ -950,7 +954,8 @@ int arnold_debug_sincos(arnold_ctx* c, int precision, int64_t n, const double* x
   if (!c || !x || !s || !co || n <= 0) return ARNOLD_EINVAL;
   ACHECK(cudaSetDevice(c->device));
   cudaError_t e = precision == ARNOLD_FP32C  ? launch_debug_sincos32(x, s, co, n, c->scf, c->stream)
-                 : precision == ARNOLD_DF64 ? launch_debug_sincos_df(x, s, co, n, c->scd, c->stream)
+                 : precision == ARNOLD_DF64 ? launch_debug_sincos_df(x, s, co, n, c->scd, false, c->stream)
+                 : precision == ARNOLD_DF64F ? launch_debug_sincos_df(x, s, co, n, c->scd, true, c->stream)
                                             : launch_debug_sincos64(x, s, co, n, c->sc, c->th, c->stream);
   ACHECK(e);
   c->launches++;

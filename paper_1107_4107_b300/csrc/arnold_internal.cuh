@@ -125,9 +125,10 @@ cudaError_t launch_iterate_fp64(const IterArgs& a, int scheme, bool tangent, int
                                 cudaStream_t st);
 cudaError_t launch_iterate_fp32c(const IterArgs& a, int scheme, bool tangent, int block, int grid,
                                  cudaStream_t st);
-cudaError_t launch_iterate_df64(const IterArgs& a, int scheme, bool tangent, int block, int grid, cudaStream_t st);
+cudaError_t launch_iterate_df64(const IterArgs& a, int scheme, bool tangent, bool fast, int block, int grid,
+                                cudaStream_t st);
 int fp64_blocks_per_sm(int scheme, bool tangent, int block);
-int df64_blocks_per_sm(int scheme, bool tangent, int block);
+int df64_blocks_per_sm(int scheme, bool tangent, bool fast, int block);
 int fp32c_blocks_per_sm(int scheme, bool tangent, int block);
 
 }  // namespace arnold

@@ -86,7 +86,7 @@ cudaError_t launch_init_grid(const InitArgs& a, int grid, int block, cudaStream_
 cudaError_t launch_indicator(const ReadArgs& a, int grid, int block, cudaStream_t st);
 cudaError_t launch_debug_sincos64(const double* x, double* s, double* c, long long n, const double2* sc,
                                   const double* th, cudaStream_t st);
-cudaError_t launch_debug_sincos_df(const double* x, double* s, double* c, long long n, const float4* scd,
+cudaError_t launch_debug_sincos_df(const double* x, double* s, double* c, long long n, const float4* scd, bool fast,
                                    cudaStream_t st);
 cudaError_t launch_debug_sincos32(const double* x, double* s, double* c, long long n, const float2* scf,
                                   cudaStream_t st);

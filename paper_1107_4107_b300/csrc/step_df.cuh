@@ -126,6 +126,34 @@ __device__ __forceinline__ void sincos_df(const Pair& x, const float4* __restric
   }
 }
 
+// sin and cos of the pair x to ~3e-10 absolute (the "DF64F" mode): the same
+// table, but the reduced argument r = x - theta_j in FP32 (one rounding per
+// FMA at |r| <= D/2, ~1e-10), sin r - r = -r^3/6 folded into r, and the small
+// terms C (r - r^3/6) + S cm and C cm - S (r - r^3/6) (|.| <= 1.6e-3) in FP32,
+// joined to the table's pair (S, C) by TwoSum.  The error is that of r and of
+// the small terms' rounding; the products and sums that use the result stay
+// double-float.
+__device__ __forceinline__ void sincos_df_fast(const Pair& x, const float4* __restrict__ tab, const TabDF& tb,
+                                               Pair& s, Pair& c) {
+  const float t = fmaf(x.hi, tb.inv_d, 12582912.0f);
+  const float jf = __fsub_rn(t, 12582912.0f);
+  const int j = (__float_as_int(t) - 0x4B400000) & tb.mask;
+  float r = fmaf(-jf, tb.d1, x.hi);                         // exact
+  r = fmaf(-jf, tb.d2, r);
+  r = fmaf(-jf, tb.d3, r);
+  r = __fadd_rn(r, x.lo);
+  const float cm = __fmul_rn(-0.5f, __fmul_rn(r, r));      // cos r - 1 (r^4/24 < 3e-13 dropped)
+  const float rs = fmaf(__fmul_rn(r, 0.333333343f), cm, r); // r - r^3/6 = sin r (r^5/120 < 1e-16 dropped)
+  const float4 e = tab[j];   // (S hi, S lo, C hi, C lo)
+  const float qs = fmaf(e.z, rs, __fmul_rn(e.x, cm));
+  const float qc = fmaf(-e.x, rs, __fmul_rn(e.z, cm));
+  float h, l;
+  two_sum(e.x, qs, h, l);
+  s = {h, __fadd_rn(l, e.y)};
+  two_sum(e.z, qc, h, l);
+  c = {h, __fadd_rn(l, e.w)};
+}
+
 // State of one DF64 trajectory: phase-space state and tangent as float pairs
 // (~48 bits each), laps as integers.
 struct TrajDF {
@@ -158,13 +186,20 @@ __device__ __forceinline__ void drift_df(TrajDF& t, float sh, float sl) {
 // pair).  The tangent update (the Hessian of Eq. 2 applied to the tangent) is
 // double-float as well, coefficients and accumulation: on a regular orbit the
 // tangent map is a shear, and FP32 coefficients or FP32 accumulation bias its
-// growth over 1e6 steps (the chi field then drifts by percents).
-template <bool TAN>
+// growth over 1e6 steps (the chi field then drifts by percents).  FAST takes
+// the sines and cosines from sincos_df_fast (~3e-10) instead of sincos_df.
+template <bool TAN, bool FAST = false>
 __device__ __forceinline__ void kick_df(TrajDF& t, const Pair& k2, const float4* tab, const TabDF& tb) {
   Pair su, cu, sv, cv, sz, cz;
-  sincos_df(t.u, tab, tb, su, cu);
-  sincos_df(t.v, tab, tb, sv, cv);
-  sincos_df(t.z, tab, tb, sz, cz);
+  if (FAST) {
+    sincos_df_fast(t.u, tab, tb, su, cu);
+    sincos_df_fast(t.v, tab, tb, sv, cv);
+    sincos_df_fast(t.z, tab, tb, sz, cz);
+  } else {
+    sincos_df(t.u, tab, tb, su, cu);
+    sincos_df(t.v, tab, tb, sv, cv);
+    sincos_df(t.z, tab, tb, sz, cz);
+  }
   const Pair kc = df_mul_u(k2, cz);
   const Pair G = df_mul_u(kc, cz);    // k2 c_z^2
   const Pair Sp = df_mul_u(kc, sz);   // k2 s_z c_z

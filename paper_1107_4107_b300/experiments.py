@@ -177,7 +177,8 @@ def timed_web_experiment(n: int, E: float = 400.0, window_T: float = 50.0, preci
             "map_steps_per_s": n * steps / t_prop, "histogram_s": t_hist, "counted": int(counts.sum())}
 
 
-def scan_agreement(E: float = 400.0, steps: int = 1_000_000, G: int = 2048, precisions=("fp64", "fp32c", "df64"),
+def scan_agreement(E: float = 400.0, steps: int = 1_000_000, G: int = 2048,
+                   precisions=("fp64", "fp32c", "df64", "df64f"),
                    seed: int = 0, device: int = 0) -> list[dict]:
     """The Arnold-web scan of Sec. IV on a G x G grid of initial actions at
     energy E, run to `steps` steps in every precision mode from the same initial
@@ -246,8 +247,9 @@ def main(argv=None):
     import sys
     args = sys.argv[1:] if argv is None else argv
     if args and args[0] == "scan" and len(args) >= 3:
+        precs = tuple(args[4].split(",")) if len(args) > 4 else ("fp64", "fp32c", "df64", "df64f")
         for r in scan_agreement(E=float(args[1]), steps=int(float(args[2])),
-                                G=int(args[3]) if len(args) > 3 else 2048):
+                                G=int(args[3]) if len(args) > 3 else 2048, precisions=precs):
             print(json.dumps(r), flush=True)
         return
     if args and args[0] == "diffusion" and len(args) >= 2:

@@ -15,7 +15,7 @@ import json
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32c", "df64"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32c", "df64", "df64f"])
     ap.add_argument("--n", type=int, default=1 << 20)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--launches", type=int, default=3)

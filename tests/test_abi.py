@@ -67,7 +67,7 @@ def test_create_rejects_bad_arguments_before_cuda(L):
     base = _lib.Params()
     L.arnold_params_default(ctypes.byref(base))
     bad = []
-    for field, val in (("h", 0.0), ("scheme", 7), ("precision", 3), ("renorm_every", 0), ("window", -1),
+    for field, val in (("h", 0.0), ("scheme", 7), ("precision", 4), ("renorm_every", 0), ("window", -1),
                        ("chaos_kappa", 0.0), ("block_size", 48), ("tangent", 2), ("megno", 2),
                        ("reserved", 1)):
         p = _lib.Params.from_buffer_copy(base)

@@ -43,7 +43,7 @@ def test_scan_agreement_runs_all_modes_from_the_same_ics():
     (short horizon: near-identical classes)."""
     from paper_1107_4107_b300.experiments import scan_agreement
     rows = scan_agreement(E=40.0, steps=300, G=64)
-    assert [r["precision"] for r in rows] == ["fp64", "fp32c", "df64"]
+    assert [r["precision"] for r in rows] == ["fp64", "fp32c", "df64", "df64f"]
     for r in rows[1:]:
         assert r["class_agreement"] >= 0.99 and r["hist_l1"] <= 1e-2
     assert all(r["map_steps_per_s"] > 0 for r in rows)

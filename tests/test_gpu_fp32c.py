@@ -114,7 +114,7 @@ def test_fp32c_reduce64_variant_matches(tmp_path):
     assert rel_err(outs[0], outs[1]) < 1e-6
 
 
-@pytest.mark.parametrize("precision", ["fp32c", "df64"])
+@pytest.mark.parametrize("precision", ["fp32c", "df64", "df64f"])
 def test_pair_state_readout_angles_and_energy_error(precision):
     """Pair states hold angles unreduced between exact reductions (FP32C up to 64 rad):
     the read-out must still give X in [0, 2pi) and dE = |H(X, P) - H(X0, P0)| evaluated

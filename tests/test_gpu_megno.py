@@ -10,8 +10,9 @@ MEGNO to 4e-10.  FP32C carries the tangent in FP32, whose log-sum error grows
 about linearly in the step count (bar below); DF64 carries it in double-float
 (~48 bits), held to the FP64 bars x 2^5.  The tests check the
 summation-by-parts bound itself against both sides' recorded log-sum
-histories.  The eps = 0 closed form has no Hessian, so there FP32C is held to
-4e-6 t and DF64 to 32 x 1e-12.
+histories.  DF64F (double-float with a ~3e-10 sincos) holds its log sums to
+its 1000-step FTLE bar times t.  The eps = 0 closed form has no Hessian, so
+there FP32C is held to 4e-6 t and DF64 and DF64F to 32 x 1e-12.
 """
 import math
 
@@ -69,7 +70,7 @@ def test_megno_fp64_low_growth_cells_long():
     assert _megno_err(ens, st, low) < 4e-10
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32c", "df64"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32c", "df64", "df64f"])
 def test_megno_free_flow_closed_form(precision):
     """eps = 0: |w(t)|^2 = ((1 + t)^2 + 1) / 2 for w0 = (1, ..., 1)/sqrt 6 (Sec. II
     free rotation), independent of the oracle."""
@@ -83,7 +84,7 @@ def test_megno_free_flow_closed_form(precision):
     lnN = 0.5 * np.log(((1.0 + t) ** 2 + 1.0) / 2.0)
     j = np.arange(1, m + 1)
     Y = 2.0 * np.cumsum(j * np.diff(lnN)) / j
-    tol = {"fp64": 1e-12, "df64": 32e-12, "fp32c": 4e-6 * (R * m * h)}[precision]
+    tol = {"fp64": 1e-12, "df64": 32e-12, "df64f": 32e-12, "fp32c": 4e-6 * (R * m * h)}[precision]
     assert rel_err(ens.indicator("megno_y"), np.full(64, Y[-1])) < tol
     assert rel_err(ens.indicator("megno"), np.full(64, Y.mean())) < tol
 
@@ -95,7 +96,7 @@ def test_megno_free_flow_closed_form(precision):
 LOG_BAR_PER_STEP = 2.0 * 15.0 * 2.0 ** -24
 
 
-@pytest.mark.parametrize("precision", ["fp32c", "df64"])
+@pytest.mark.parametrize("precision", ["fp32c", "df64", "df64f"])
 @pytest.mark.parametrize("n", [33, 700])
 def test_megno_pair_modes_vs_oracle(precision, n):
     """Ragged sizes (padding slots repeat the last trajectory and must not add to its
@@ -120,7 +121,9 @@ def test_megno_pair_modes_vs_oracle(precision, n):
         d = np.abs(ens.indicator(kind) - ref)
         assert np.all(d <= 4.0 * dL + 1e-12 * (1.0 + np.abs(ref))), kind
     worst = float(dL[low].max())
-    bar = LOG_BAR_PER_STEP * R * m if precision == "fp32c" else 32 * 1e-10
+    # FP32C: the FP32-tangent bar; DF64: the FP64 low-growth bar x 2^5; DF64F: its
+    # 1000-step FTLE bar times t
+    bar = {"fp32c": LOG_BAR_PER_STEP * R * m, "df64": 32 * 1e-10, "df64f": 1e-8 * R * m * 0.02 * math.pi}[precision]
     print(f"{precision} n={n}: max |d log sum| on low-growth cells = {worst:.2e} (bar {bar:.2e})")
     assert worst < bar, worst
     # the last trajectory (the one padding slots repeat) holds the same bound
@@ -128,7 +131,7 @@ def test_megno_pair_modes_vs_oracle(precision, n):
     assert abs(ens.indicator("megno")[-1] - ref_last) <= 4.0 * dL[-1] + 1e-12 * (1.0 + abs(ref_last))
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32c", "df64"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32c", "df64", "df64f"])
 def test_megno_launch_split_and_resume_bitwise(precision):
     X, P = inputs.box(300, seed=25)
     ref = _ens(300, renorm_every=10, precision=precision)

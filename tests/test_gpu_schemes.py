@@ -31,7 +31,7 @@ def _ens(n, **kw):
     return ArnoldEnsemble(n, **kw)
 
 
-@pytest.mark.parametrize("precision,bar", [("fp32c", 3e-7), ("df64", 3e-11)])
+@pytest.mark.parametrize("precision,bar", [("fp32c", 3e-7), ("df64", 3e-11), ("df64f", 1e-9)])
 @pytest.mark.parametrize("scheme", SCHEMES)
 def test_pair_modes_other_schemes_vs_oracle(precision, bar, scheme):
     n, h, R = 333, 0.05, 7

@@ -25,7 +25,7 @@ def _ens(n, **kw):
     return ArnoldEnsemble(n, **kw)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32c", "df64"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32c", "df64", "df64f"])
 def test_snapshots_equal_per_window_reads(torch, precision):
     n, W, k = 777, 50, 5
     X, P = inputs.box(n, seed=41)
