@@ -39,7 +39,11 @@ def _ptr_kind(a):
 
 
 class ArnoldEnsemble:
-    """n independent trajectories held on one GPU (library-owned device memory)."""
+    """n independent trajectories held on one GPU (library-owned device memory).
+
+    precision: "fp64" (FP64 accuracy), "fp32c" (compensated FP32, FP32 tangent),
+    "df64" (double-float state, kicks and tangent) or "df64f" (double-float with
+    a ~3e-10 sincos); scheme: "yoshida6a", "triplejump6" or "leapfrog2"."""
 
     def __init__(self, n: int, eps: float = 1.0, h: float | None = None, scheme: str = "yoshida6a",
                  precision: str = "fp64", tangent: bool = True, renorm_every: int = 100, window: int = 0,

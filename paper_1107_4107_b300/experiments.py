@@ -241,7 +241,7 @@ def main(argv=None):
            -> one timed web experiment (sphere, 5000 steps, F) as a JSON line
        python -m paper_1107_4107_b300.experiments diffusion PRECISION
            -> the Fig. 4 diffusion run's rate (32,000 trajectories, E = 15)
-       python -m paper_1107_4107_b300.experiments scan E STEPS [G]
+       python -m paper_1107_4107_b300.experiments scan E STEPS [G [PREC,PREC,...]]
            -> the G x G scan in FP64, FP32C and DF64 with agreement vs FP64"""
     import json
     import sys
@@ -262,7 +262,7 @@ def main(argv=None):
         return
     if not args or args[0] != "sweep":
         raise SystemExit("usage: python -m paper_1107_4107_b300.experiments sweep | web N PRECISION [E] | "
-                         "diffusion PRECISION | scan E STEPS [G]")
+                         "diffusion PRECISION | scan E STEPS [G [PRECISIONS]]")
     steps = {"fp64": (200, 50), "fp32c": (1000, 400), "df64": (400, 100)}   # (N <= 606,208, larger N)
     for prec in ("fp64", "fp32c", "df64"):
         small = [n for n in SWEEP_NS if n <= 606208]
