@@ -235,14 +235,14 @@ def timed_diffusion_rate(n: int = 32000, E: float = 15.0, steps: int = 50000, pr
 
 
 def main(argv=None):
-    """python -m paper_1107_4107_b300.experiments sweep
-           -> JSON lines of throughput_vs_n
+    """python -m paper_1107_4107_b300.experiments sweep [PREC,PREC,...]
+           -> JSON lines of throughput_vs_n (default: every precision mode)
        python -m paper_1107_4107_b300.experiments web N PRECISION [E]
            -> one timed web experiment (sphere, 5000 steps, F) as a JSON line
        python -m paper_1107_4107_b300.experiments diffusion PRECISION
            -> the Fig. 4 diffusion run's rate (32,000 trajectories, E = 15)
        python -m paper_1107_4107_b300.experiments scan E STEPS [G [PREC,PREC,...]]
-           -> the G x G scan in FP64, FP32C and DF64 with agreement vs FP64"""
+           -> the G x G scan in FP64, FP32C, DF64 and DF64F (or the listed modes) with agreement vs FP64"""
     import json
     import sys
     args = sys.argv[1:] if argv is None else argv
@@ -261,10 +261,10 @@ def main(argv=None):
         print(json.dumps(r), flush=True)
         return
     if not args or args[0] != "sweep":
-        raise SystemExit("usage: python -m paper_1107_4107_b300.experiments sweep | web N PRECISION [E] | "
+        raise SystemExit("usage: python -m paper_1107_4107_b300.experiments sweep [PRECISIONS] | web N PRECISION [E] | "
                          "diffusion PRECISION | scan E STEPS [G [PRECISIONS]]")
-    steps = {"fp64": (200, 50), "fp32c": (1000, 400), "df64": (400, 100)}   # (N <= 606,208, larger N)
-    for prec in ("fp64", "fp32c", "df64"):
+    steps = {"fp64": (200, 50), "fp32c": (1000, 400), "df64": (400, 100), "df64f": (600, 150)}   # (N <= 606,208, larger N)
+    for prec in (args[1].split(",") if len(args) > 1 else ("fp64", "fp32c", "df64", "df64f")):
         small = [n for n in SWEEP_NS if n <= 606208]
         big = [n for n in SWEEP_NS if n > 606208]
         rows = throughput_vs_n(small, steps=steps[prec][0], precision=prec)
