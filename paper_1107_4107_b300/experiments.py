@@ -74,20 +74,22 @@ def diffusion_from_w(n: int = 32000, E: float = 15.0, sigma: float = 0.01, windo
     be <= 0 there).  F of V over windows of window_T is accumulated between
     consecutive snapshot times (time-averaged F).  With ckpt_path the state is
     saved after every window and a rerun resumes from it."""
+    import torch
     h = paper_h() if h is None else h
     W = math.sqrt(E)
     w_steps = int(round(window_T * T / h))
     e = init_gaussian_valid(n, E, (W, W), sigma, seed, precision=precision, window=w_steps, h=h, device=device)
     done_windows = 0
     maps = []
-    acc = np.zeros((n_cos, n_phi), dtype=np.uint64)
+    # F accumulates on the device between snapshots (no host round trip per window)
+    acc = torch.zeros((n_cos, n_phi), dtype=torch.int64, device=f"cuda:{device}")
     if ckpt_path and os.path.exists(ckpt_path):
         blob = open(ckpt_path, "rb").read()
         e.restore(blob[:-16])
         done_windows = int(np.frombuffer(blob[-16:-8], dtype=np.int64)[0])
         acc_path = ckpt_path + ".acc.npy"
         if os.path.exists(acc_path):
-            acc = np.load(acc_path)
+            acc.copy_(torch.from_numpy(np.load(acc_path).astype(np.int64)))
     bounds = [int(round(s * T / h / w_steps)) for s in snapshots_T]
     k = 0
     while k < len(bounds) and bounds[k] <= done_windows:
@@ -97,13 +99,13 @@ def diffusion_from_w(n: int = 32000, E: float = 15.0, sigma: float = 0.01, windo
         done_windows += 1
         e.velocity_histogram(n_cos, n_phi, out=acc, accumulate=True)
         if done_windows == bounds[k]:
-            maps.append({"t_T": snapshots_T[k], "counts": acc.copy()})
-            acc[:] = 0
+            maps.append({"t_T": snapshots_T[k], "counts": acc.cpu().numpy().astype(np.uint64)})
+            acc.zero_()
             k += 1
         if ckpt_path:
             with open(ckpt_path, "wb") as f:
                 f.write(e.checkpoint() + np.array([done_windows, 0], dtype=np.int64).tobytes())
-            np.save(ckpt_path + ".acc.npy", acc)
+            np.save(ckpt_path + ".acc.npy", acc.cpu().numpy().astype(np.uint64))
     e.sync()
     return {"maps": maps, "windows": done_windows, "n": n, "E": E, "window_steps": w_steps}
 
@@ -241,6 +243,9 @@ def main(argv=None):
            -> one timed web experiment (sphere, 5000 steps, F) as a JSON line
        python -m paper_1107_4107_b300.experiments diffusion PRECISION
            -> the Fig. 4 diffusion run's rate (32,000 trajectories, E = 15)
+       python -m paper_1107_4107_b300.experiments fig4 PRECISION T_END [OUT.npz]
+           -> the Fig. 4 run itself to T_END periods: F time-averaged between
+              the snapshot times 1e2, 1e3, ... T (saved to OUT.npz), wall time
        python -m paper_1107_4107_b300.experiments scan E STEPS [G [PREC,PREC,...]]
            -> the G x G scan in FP64, FP32C, DF64 and DF64F (or the listed modes) with agreement vs FP64"""
     import json
@@ -252,6 +257,21 @@ def main(argv=None):
                                 G=int(args[3]) if len(args) > 3 else 2048, precisions=precs):
             print(json.dumps(r), flush=True)
         return
+    if args and args[0] == "fig4" and len(args) >= 3:
+        import time
+        t_end = float(args[2])
+        snaps = tuple(t for t in (1e2, 1e3, 1e4, 1e5, 1e6, 1e7) if t <= t_end)
+        t0 = time.perf_counter()
+        r = diffusion_from_w(precision=args[1], snapshots_T=snaps)
+        wall = time.perf_counter() - t0
+        if len(args) > 3:
+            np.savez_compressed(args[3], **{f"F_{int(m['t_T'])}T": m["counts"] for m in r["maps"]})
+        print(json.dumps({"precision": args[1], "n": r["n"], "E": r["E"], "t_end_T": t_end,
+                          "steps": r["windows"] * r["window_steps"], "wall_s": wall,
+                          "map_steps_per_s": r["n"] * r["windows"] * r["window_steps"] / wall,
+                          "snapshots": [{"t_T": m["t_T"], "occupied_cells": int(np.count_nonzero(m["counts"])),
+                                         "counts": int(m["counts"].sum())} for m in r["maps"]]}), flush=True)
+        return
     if args and args[0] == "diffusion" and len(args) >= 2:
         print(json.dumps(timed_diffusion_rate(precision=args[1])), flush=True)
         return
@@ -262,7 +282,7 @@ def main(argv=None):
         return
     if not args or args[0] != "sweep":
         raise SystemExit("usage: python -m paper_1107_4107_b300.experiments sweep [PRECISIONS] | web N PRECISION [E] | "
-                         "diffusion PRECISION | scan E STEPS [G [PRECISIONS]]")
+                         "diffusion PRECISION | fig4 PRECISION T_END [OUT] | scan E STEPS [G [PRECISIONS]]")
     steps = {"fp64": (200, 50), "fp32c": (1000, 400), "df64": (400, 100), "df64f": (600, 150)}   # (N <= 606,208, larger N)
     for prec in (args[1].split(",") if len(args) > 1 else ("fp64", "fp32c", "df64", "df64f")):
         small = [n for n in SWEEP_NS if n <= 606208]
