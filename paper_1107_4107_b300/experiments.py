@@ -107,7 +107,8 @@ def diffusion_from_w(n: int = 32000, E: float = 15.0, sigma: float = 0.01, windo
                 f.write(e.checkpoint() + np.array([done_windows, 0], dtype=np.int64).tobytes())
             np.save(ckpt_path + ".acc.npy", acc.cpu().numpy().astype(np.uint64))
     e.sync()
-    return {"maps": maps, "windows": done_windows, "n": n, "E": E, "window_steps": w_steps}
+    return {"maps": maps, "windows": done_windows, "n": n, "E": E, "window_steps": w_steps,
+            "dE_max": float(e.indicator("dE_max").max())}
 
 
 def init_gaussian_valid(n: int, E: float, center, sigma: float, seed: int, **kw) -> ArnoldEnsemble:
@@ -269,6 +270,7 @@ def main(argv=None):
         print(json.dumps({"precision": args[1], "n": r["n"], "E": r["E"], "t_end_T": t_end,
                           "steps": r["windows"] * r["window_steps"], "wall_s": wall,
                           "map_steps_per_s": r["n"] * r["windows"] * r["window_steps"] / wall,
+                          "dE_max": r["dE_max"],
                           "snapshots": [{"t_T": m["t_T"], "occupied_cells": int(np.count_nonzero(m["counts"])),
                                          "counts": int(m["counts"].sum())} for m in r["maps"]]}), flush=True)
         return
