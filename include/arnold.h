@@ -28,6 +28,9 @@
  *     that stream; others return before the GPU finishes.  An error raised by
  *     a kernel is reported by the next call that synchronises.
  *   - Threads: a context may be used from one host thread at a time.
+ *   - Current device: calls on a context (or batch) leave that context's device
+ *     current in the calling host thread; arnold_stats_arrays_noalloc restores
+ *     the caller's.
  */
 #ifndef ARNOLD_H
 #define ARNOLD_H
@@ -48,7 +51,7 @@ extern "C" {
 #define ARNOLD_ENONFINITE   -5  /* the state became NaN/Inf (checked when results are read)         */
 #define ARNOLD_EUNSUPPORTED -6  /* combination not built (e.g. no CUDA device)                      */
 #define ARNOLD_ESTATE       -7  /* call out of order (e.g. arnold_grad before arnold_forward_ckpt)  */
-#define ARNOLD_ERANGE       -8  /* outside the precision mode's range (h |q| per step > 9 for DF64 and DF64F, > 400 for FP32C) */
+#define ARNOLD_ERANGE       -8  /* outside the precision mode's range (h |q| per step > 160 for DF64 and DF64F, > 400 for FP32C) */
 
 /* ---- enums --------------------------------------------------------------- */
 /* Integrators (Sec. III names a sixth-order symplectic scheme whose reference
@@ -62,10 +65,11 @@ extern "C" {
 #define ARNOLD_FP32C 1  /* compensated FP32: float-pair angles (held in a [1024, 2048) rad window, whole
                            turns removed exactly) and momenta, two-sum updates; FP64 logs and energy     */
 #define ARNOLD_DF64  2  /* double-float: state, kicks and tangent in float pairs (~48-bit), FP64-grade
-                           trajectories on the FP32 pipes.  No adjoint or batch.                        */
+                           trajectories on the FP32 pipes.  No adjoint.                                 */
 #define ARNOLD_DF64F 3  /* DF64 with a faster sincos: the same double-float state, products, sums and
                            tangent, but sines and cosines to ~3e-10 (FP32 reduced argument joined to the
-                           table's float pairs).  No adjoint or batch.                                   */
+                           table's float pairs).  The compensated-FP32 mode for long horizons: its 1e6-step
+                           indicator field matches FP64's.  No adjoint.                                  */
 
 #define ARNOLD_HOST   0
 #define ARNOLD_DEVICE 1
@@ -242,7 +246,8 @@ int arnold_stats_arrays(arnold_ctx* ctx, int64_t n, const double* chi, const dou
  *   n, chi, dE, p, t, kappa, out: as arnold_stats_arrays (device f64 inputs,
  *   dE may be NULL, host output struct); synchronises the stream.
  * The first call on a device looks up the array's device address (set-up);
- * make that first call before any stream capture.  All calls share the array:
+ * make that first call before any stream capture.  The caller's current
+ * device is the same after the call as before it.  All calls share the array:
  * calls whose kernels overlap on the GPU race and must be serialised by the
  * caller.  Errors: EINVAL (NULL, n <= 0 or n > ARNOLD_NOALLOC_MAX_N, kappa <= 0,
  * t == 0, bad device), EUNSUPPORTED, ECUDA. */
@@ -281,8 +286,9 @@ int arnold_grad(arnold_ctx* ctx, const double* dL_dx, const double* dL_dp, doubl
  * Many parameter sets (the scans of Sec. IV repeated over a grid of (K, eps)),
  * each a grid slice of initial actions with its own ensemble size and step
  * count, advanced together by one CUDA-graph launch of persistent kernels in
- * compensated FP32 (ARNOLD_FP32C).  Each set's trajectories are bit-identical
- * to those of a single FP32C context with the same parameters. */
+ * compensated FP32 (ARNOLD_FP32C) or double-float (ARNOLD_DF64F, ARNOLD_DF64).
+ * Each set's trajectories are bit-identical to those of a single context of
+ * the same precision with the same parameters. */
 typedef struct arnold_batch_set {
   double   eps;       /* eps of Eq. 1                                         */
   double   h;         /* composite step (K = eps h^2)                         */
@@ -294,7 +300,8 @@ typedef struct arnold_batch_set {
 
 typedef struct arnold_batch_tuning {
   int32_t block_size;       /* threads per block: multiple of 32 in [32, 256]        */
-  int32_t traj_per_thread;  /* 1 or 2 trajectories advanced interleaved per thread   */
+  int32_t traj_per_thread;  /* 1 or 2 trajectories advanced interleaved per thread
+                               (FP32C); 1 for DF64 and DF64F                         */
   int32_t renorm_every;     /* R >= 1 for every set                                  */
   int32_t epoch_ms;         /* target GPU time of one persistent launch (ms)         */
 } arnold_batch_tuning;
@@ -305,9 +312,11 @@ typedef struct arnold_batch arnold_batch;
 void arnold_batch_tuning_default(arnold_batch_tuning* t);
 
 /* Create a batch of n_sets sets (allocates every set's device state and plans
- * the epochs).  tuning NULL = defaults.  Errors: EINVAL, ENOMEM, ECUDA,
+ * the epochs).  precision: ARNOLD_FP32C, ARNOLD_DF64F or ARNOLD_DF64.  tuning
+ * NULL = defaults.  Errors: EINVAL (bad set, precision ARNOLD_FP64,
+ * traj_per_thread != 1 with a double-float precision), ENOMEM, ECUDA,
  * EUNSUPPORTED. */
-int arnold_batch_create(const arnold_batch_set* sets, int n_sets, int scheme, int tangent,
+int arnold_batch_create(const arnold_batch_set* sets, int n_sets, int scheme, int precision, int tangent,
                         const arnold_batch_tuning* tuning, int device, void* cuda_stream,
                         arnold_batch** out);
 
@@ -333,15 +342,19 @@ void arnold_batch_destroy(arnold_batch* b);
 /* ---- checkpoint / resume ----------------------------------------------------
  * The complete per-trajectory state (phase-space state, tangent, laps, window
  * references, log sums, energy references and maxima, V, MEGNO sums when
- * enabled) plus the step counter, so that a run resumed from a checkpoint
- * continues bit for bit as if uninterrupted (the paper's 24 h runs, Sec. IV,
- * motivate it).  Layout: a 64-byte header (magic "ARNOLDC1", precision,
- * tangent, n, steps, scheme, megno, eps, h) followed by the device arrays.  The buffer is host memory owned by
- * the caller. */
+ * enabled, area-tracking flags when tracking is on) plus the step counter, so
+ * that a run resumed from a checkpoint continues bit for bit as if
+ * uninterrupted (the paper's 24 h runs, Sec. IV, motivate it).  Layout: a
+ * 128-byte header (magic "ARNOLDC2", precision, tangent, n, steps, scheme,
+ * megno, eps, h, tracking on/off and the tracked patch) followed by the device
+ * arrays.  The buffer is host memory owned by the caller. */
 int arnold_checkpoint_size(const arnold_ctx* ctx, size_t* bytes);
 /* Synchronises.  Errors: EINVAL (NULL, bytes too small), ECUDA. */
 int arnold_checkpoint_save(arnold_ctx* ctx, void* host_buf, size_t bytes);
-/* The context must have the same n, precision, tangent, scheme, megno, eps and h.
+/* The context must have the same n, precision, tangent, scheme, megno, eps and h,
+ * and the same area tracking: off in both, or on in both with the same patch
+ * (call arnold_track_patch on a fresh context before loading a tracked
+ * checkpoint; the flags are then restored).
  * Errors: EINVAL (mismatch, bad magic, size), ECUDA. */
 int arnold_checkpoint_load(arnold_ctx* ctx, const void* host_buf, size_t bytes);
 

@@ -79,7 +79,8 @@ SIGNATURES = {
     "arnold_grad": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, ctypes.c_int]),
     "arnold_batch_tuning_default": (None, [ctypes.POINTER(BatchTuning)]),
     "arnold_batch_create": (ctypes.c_int, [ctypes.POINTER(BatchSet), ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                           ctypes.POINTER(BatchTuning), ctypes.c_int, vp, ctypes.POINTER(vp)]),
+                                           ctypes.c_int, ctypes.POINTER(BatchTuning), ctypes.c_int, vp,
+                                           ctypes.POINTER(vp)]),
     "arnold_batch_init": (ctypes.c_int, [vp]),
     "arnold_batch_run": (ctypes.c_int, [vp]),
     "arnold_batch_indicator": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int]),

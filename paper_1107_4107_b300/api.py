@@ -276,10 +276,14 @@ def _map_function():
             """(X0, P0, h, eps) -> (X_N unwrapped, P_N) on CUDA tensors [3][n]; the
             backward pass is the CUDA adjoint (arnold_grad) over the sqrt(N)
             checkpoints the forward pass stored.  h and eps may be floats or
-            0-d tensors; their gradients are returned as 0-d tensors."""
+            0-d tensors; a tensor gets its gradient as a 0-d tensor, a float
+            none."""
 
             @staticmethod
             def forward(ctx, X0, P0, h, eps, n_steps, ckpt_every, precision, scheme):
+                # autograd accepts a gradient only for tensor inputs
+                ctx.h_is_tensor = torch.is_tensor(h)
+                ctx.eps_is_tensor = torch.is_tensor(eps)
                 n = X0.shape[1]
                 ens = ArnoldEnsemble(n, eps=float(eps), h=float(h), scheme=scheme, precision=precision,
                                      tangent=False, device=X0.device.index or 0)
@@ -299,7 +303,9 @@ def _map_function():
                 ens.close()   # the checkpoints are spent: one backward per forward
                 ctx.ens = None
                 dev = gX.device
-                return gx0, gp0, gh.to(dev).reshape(()), ge.to(dev).reshape(()), None, None, None, None
+                gh = gh.to(dev).reshape(()) if ctx.h_is_tensor else None
+                ge = ge.to(dev).reshape(()) if ctx.eps_is_tensor else None
+                return gx0, gp0, gh, ge, None, None, None, None
 
         _MAP_FN = ArnoldMap
     return _MAP_FN
@@ -319,14 +325,16 @@ def arnold_map(X0, P0, h, eps, n_steps: int, ckpt_every: int = 0, precision: str
 
 
 class ArnoldBatch:
-    """Many parameter sets advanced by one CUDA-graph launch (FP32C).
+    """Many parameter sets advanced by one CUDA-graph launch.
 
     sets: list of dicts with eps, h, E, G, n_steps, seed (see arnold_batch_set).
-    tuning: dict with block_size, traj_per_thread, renorm_every, epoch_ms, or
-    None for the library defaults (paper_1107_4107_b300.tune picks one)."""
+    precision: "fp32c" (short horizons), "df64f" (the long-horizon compensated
+    mode) or "df64".  tuning: dict with block_size, traj_per_thread,
+    renorm_every, epoch_ms, or None for the library defaults
+    (paper_1107_4107_b300.tune picks one)."""
 
     def __init__(self, sets, scheme: str = "yoshida6a", tangent: bool = True, tuning: dict | None = None,
-                 device: int = 0, stream=None):
+                 device: int = 0, stream=None, precision: str = "fp32c"):
         L = _lib.lib()
         arr = (_lib.BatchSet * len(sets))()
         for k, q in enumerate(sets):
@@ -340,9 +348,11 @@ class ArnoldBatch:
             import torch
             stream = torch.cuda.current_stream(device).cuda_stream
         h = ctypes.c_void_p()
-        check(L.arnold_batch_create(arr, len(sets), _lib.SCHEMES[scheme], int(bool(tangent)), ctypes.byref(tu), device,
-                                    ctypes.c_void_p(stream), ctypes.byref(h)), "arnold_batch_create")
+        check(L.arnold_batch_create(arr, len(sets), _lib.SCHEMES[scheme], _lib.PRECISIONS[precision],
+                                    int(bool(tangent)), ctypes.byref(tu), device, ctypes.c_void_p(stream),
+                                    ctypes.byref(h)), "arnold_batch_create")
         self._h = h
+        self.precision = precision
         self.sets = [dict(q) for q in sets]
         self.tuning = {f: getattr(tu, f) for f, _ in _lib.BatchTuning._fields_}
 

@@ -335,8 +335,8 @@ size_t indicator_bytes(int kind, long long n) {
 
 namespace arnold {
 // Accessors used by the batched launch (batch.cu).
-int ctx_run_args32(arnold_ctx* c, RunArgs32* ra, Coef32* cf, const float2** scf) {
-  if (c->prm.precision != ARNOLD_FP32C) return ARNOLD_EUNSUPPORTED;
+int ctx_run_args(arnold_ctx* c, RunArgs32* ra, StepCoef* sc, const float2** scf, const float4** scd) {
+  if (c->prm.precision == ARNOLD_FP64) return ARNOLD_EUNSUPPORTED;
   ra->s = c->s;
   ra->f = c->f;
   ra->n = c->n;
@@ -345,8 +345,9 @@ int ctx_run_args32(arnold_ctx* c, RunArgs32* ra, Coef32* cf, const float2** scf)
   ra->h = c->prm.h;
   ra->eps = c->prm.eps;
   ra->flags = c->flags;
-  *cf = coef32_from(make_coef(c->prm));
+  *sc = make_coef(c->prm);
   *scf = c->scf;
+  *scd = c->scd;
   return ARNOLD_OK;
 }
 void ctx_add_steps(arnold_ctx* c, long long s) {
@@ -850,11 +851,14 @@ struct CkptHeader {
   int64_t n, steps;
   int32_t scheme, megno;
   double eps, h;
-  int64_t reserved;
+  int32_t tracking, reserved0;   // area tracking on (1) / off (0)
+  double patch[4];               // the tracked patch (cos_lo, cos_hi, phi_lo, phi_hi) when on
+  int64_t reserved[4];
 };
-static_assert(sizeof(CkptHeader) == 64, "checkpoint header is 64 bytes");
+static_assert(sizeof(CkptHeader) == 128, "checkpoint header is 128 bytes");
 
-// (device pointer, bytes) of every array that makes up the state.
+// (device pointer, bytes) of every array that makes up the state, the
+// area-tracking flags included when tracking is on.
 static int ckpt_arrays(const arnold_ctx* c, void** ptrs, size_t* sizes) {
   const size_t n = (size_t)c->n;
   int k = 0;
@@ -875,6 +879,7 @@ static int ckpt_arrays(const arnold_ctx* c, void** ptrs, size_t* sizes) {
   add(c->s.e0, 8 * n);
   add(c->s.V, 24 * n);
   add(c->s.megno, 16 * n);
+  add(c->s.left, n);
   return k;
 }
 
@@ -895,7 +900,7 @@ int arnold_checkpoint_save(arnold_ctx* c, void* buf, size_t bytes) {
   ACHECK(cudaSetDevice(c->device));
   CkptHeader hd;
   memset(&hd, 0, sizeof hd);
-  memcpy(hd.magic, "ARNOLDC1", 8);
+  memcpy(hd.magic, "ARNOLDC2", 8);
   hd.precision = c->prm.precision;
   hd.tangent = c->prm.tangent;
   hd.n = c->n;
@@ -904,6 +909,8 @@ int arnold_checkpoint_save(arnold_ctx* c, void* buf, size_t bytes) {
   hd.megno = c->prm.megno;
   hd.eps = c->prm.eps;
   hd.h = c->prm.h;
+  hd.tracking = c->s.left != nullptr;
+  if (hd.tracking) memcpy(hd.patch, c->s.patch, sizeof hd.patch);
   memcpy(buf, &hd, sizeof hd);
   void* p[16];
   size_t sz[16];
@@ -918,13 +925,19 @@ int arnold_checkpoint_save(arnold_ctx* c, void* buf, size_t bytes) {
 }
 
 int arnold_checkpoint_load(arnold_ctx* c, const void* buf, size_t bytes) {
-  size_t need = 0;
-  if (!c || !buf || arnold_checkpoint_size(c, &need) || bytes < need) return ARNOLD_EINVAL;
+  if (!c || !buf || bytes < sizeof(CkptHeader)) return ARNOLD_EINVAL;
   CkptHeader hd;
   memcpy(&hd, buf, sizeof hd);
-  if (memcmp(hd.magic, "ARNOLDC1", 8) || hd.precision != c->prm.precision || hd.tangent != c->prm.tangent ||
-      hd.n != c->n || hd.scheme != c->prm.scheme || hd.megno != c->prm.megno || hd.eps != c->prm.eps || hd.h != c->prm.h || hd.steps < 0)
+  if (memcmp(hd.magic, "ARNOLDC2", 8) || hd.precision != c->prm.precision || hd.tangent != c->prm.tangent ||
+      hd.n != c->n || hd.scheme != c->prm.scheme || hd.megno != c->prm.megno || hd.eps != c->prm.eps ||
+      hd.h != c->prm.h || hd.steps < 0)
     return ARNOLD_EINVAL;
+  // area tracking must match: on with the same patch (arnold_track_patch first), or off
+  const int tracking = c->s.left != nullptr;
+  if (hd.tracking != tracking || (tracking && memcmp(hd.patch, c->s.patch, sizeof hd.patch)))
+    return ARNOLD_EINVAL;
+  size_t need = 0;
+  if (arnold_checkpoint_size(c, &need) || bytes < need) return ARNOLD_EINVAL;
   ACHECK(cudaSetDevice(c->device));
   void* p[16];
   size_t sz[16];

@@ -1,5 +1,6 @@
 // Batched persistent launch: many parameter sets (eps, h) with uneven ensemble
-// sizes and step counts advanced by one CUDA-graph launch (compensated FP32).
+// sizes and step counts advanced by one CUDA-graph launch, in compensated FP32
+// (FP32C) or double-float (DF64, DF64F).
 //
 // Plan (host): the run is cut into epochs of roughly equal GPU work; in epoch
 // e every set that still has steps left advances min(len_e, remaining) steps.
@@ -7,12 +8,15 @@
 // cost of one tile (longest first), so work items (set, tile) are never
 // stored: item k of the epoch maps to an entry by its tile prefix sum.
 // Kernel: one persistent launch per epoch, grid = resident blocks; each block
-// pops items with an atomic counter (no waits of any kind), loads the set's
-// arguments and runs its tile with the same per-trajectory code as the
-// single-ensemble kernel (run32.cuh), so batched and unbatched trajectories
-// are bit-identical.  The graph: one memset of the epoch counters, the epoch
-// launches in order, and a final kernel that advances the per-set step bases
-// so that a replay continues every set where the previous one stopped.
+// pops items with an atomic counter (no waits of any kind) -- thread 0 fetches
+// the next item while the block runs the current one, into the other of two
+// shared slots, so an item costs one barrier -- reads the set's arguments and
+// coefficients through read-only pointers, and runs its tile with the same
+// per-trajectory code as the single-ensemble kernels (run32.cuh, rundf.cuh),
+// so batched and unbatched trajectories are bit-identical.  The graph: one
+// memset of the epoch counters, the epoch launches in order, and a final
+// kernel that advances the per-set step bases so that a replay continues
+// every set where the previous one stopped.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -23,14 +27,16 @@
 
 #include "kernels.cuh"
 #include "run32.cuh"
+#include "rundf.cuh"
 
 struct arnold_ctx;   // defined in api.cu
 
 namespace arnold {
 
 void fp32_tab(Tab32* tb);
+void df_tab(TabDF* tb);
 // Accessors into arnold_ctx (api.cu).
-int ctx_run_args32(arnold_ctx* c, RunArgs32* ra, Coef32* cf, const float2** scf);
+int ctx_run_args(arnold_ctx* c, RunArgs32* ra, StepCoef* sc, const float2** scf, const float4** scd);
 void ctx_add_steps(arnold_ctx* c, long long s);
 long long ctx_steps(arnold_ctx* c);
 
@@ -49,6 +55,35 @@ struct EpochDesc {
   long long tiles;      // items of the epoch
 };
 
+// Locate item `item` of an epoch: its entry (set, steps) and tile index.
+__device__ __forceinline__ const EpochEntry& find_entry(const EpochEntry* __restrict__ entries, const EpochDesc& ep,
+                                                       long long item, long long& t_idx) {
+  int e = ep.first;
+  while (entries[e].tile_end <= item) ++e;   // <= 64 entries, sorted prefix
+  t_idx = item - (e > ep.first ? entries[e - 1].tile_end : 0);
+  return entries[e];
+}
+
+// Thread 0: pop the next work item into shared slot `slot` and stage its set's
+// arguments and step coefficients beside it.  A block works on slot it & 1 in iteration it
+// while thread 0 fills the other slot, which every thread last read before the
+// barrier that opened iteration it; the barrier that opens iteration it + 1
+// publishes it.  So each item costs one barrier, and the atomic's latency
+// overlaps the tile's run.
+template <typename C>
+__device__ __forceinline__ void pop_item(int* counter, const EpochDesc& ep, const EpochEntry* __restrict__ entries,
+                                         const RunArgs32* __restrict__ sets, const C* __restrict__ coefs,
+                                         long long* s_item, RunArgs32* s_ra, C* s_cf, int slot) {
+  const long long item = atomicAdd(counter, 1);
+  s_item[slot] = item;
+  if (item < ep.tiles) {
+    long long t_idx;
+    const int set = find_entry(entries, ep, item, t_idx).set;
+    s_ra[slot] = sets[set];
+    s_cf[slot] = coefs[set];
+  }
+}
+
 // Register cap: two resident blocks of 256 threads per SM.
 template <int M, bool TAN, int TPT>
 __global__ void __launch_bounds__(256, 2) k_batch_fp32c(const RunArgs32* __restrict__ sets,
@@ -59,30 +94,21 @@ __global__ void __launch_bounds__(256, 2) k_batch_fp32c(const RunArgs32* __restr
                                                      Tab32 tb) {
   extern __shared__ __align__(16) unsigned char smem[];
   float2* ssc = reinterpret_cast<float2*>(smem);
-  __shared__ long long s_item;
-  __shared__ Coef32 s_cf;
+  __shared__ long long s_item[2];
+  __shared__ RunArgs32 s_ra[2];
+  __shared__ Coef32 s_cf[2];
   for (int k = threadIdx.x; k <= tb.jmax; k += blockDim.x) ssc[k] = scf[k];
+  if (threadIdx.x == 0) pop_item(counter, ep, entries, sets, coefs, s_item, s_ra, s_cf, 0);
   const long long tile = (long long)blockDim.x * TPT;
-  for (;;) {
+  for (int it = 0;; ++it) {
     __syncthreads();
-    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
-    __syncthreads();
-    const long long item = s_item;
+    const int slot = it & 1;
+    const long long item = s_item[slot];
     if (item >= ep.tiles) break;
-    int e = ep.first;
-    while (entries[e].tile_end <= item) ++e;   // <= 64 entries, sorted prefix
-    const EpochEntry en = entries[e];
-    const long long prev_end = e > ep.first ? entries[e - 1].tile_end : 0;
-    const long long t_idx = item - prev_end;
-    const RunArgs32& ra = sets[en.set];
-    // the set's coefficients, staged in shared memory for the whole block
-    {
-      const float* src = reinterpret_cast<const float*>(coefs + en.set);
-      float* dst = reinterpret_cast<float*>(&s_cf);
-      for (int k = threadIdx.x; k < (int)(sizeof(Coef32) / sizeof(float)); k += blockDim.x) dst[k] = src[k];
-    }
-    __syncthreads();
-    const Coef32& cf = s_cf;
+    if (threadIdx.x == 0) pop_item(counter, ep, entries, sets, coefs, s_item, s_ra, s_cf, slot ^ 1);
+    long long t_idx;
+    const EpochEntry& en = find_entry(entries, ep, item, t_idx);
+    const RunArgs32& ra = s_ra[slot];
     long long idx[TPT];
     int valid = 0;
     const long long i0 = t_idx * tile;
@@ -93,7 +119,37 @@ __global__ void __launch_bounds__(256, 2) k_batch_fp32c(const RunArgs32* __restr
       idx[r] = ok ? i : ra.n - 1;
       valid |= ok ? (1 << r) : 0;
     }
-    if (valid) run_traj32<M, TAN, false, TPT>(ra, cf, idx, valid, base[en.set] + en.step0_rel, en.nsteps, ssc, tb);
+    if (valid)
+      run_traj32<M, TAN, false, TPT>(ra, s_cf[slot], idx, valid, base[en.set] + en.step0_rel, en.nsteps, ssc, tb);
+  }
+}
+
+// The same for the double-float modes (one trajectory per thread; FAST = DF64F).
+template <int M, bool TAN, bool FAST>
+__global__ void __launch_bounds__(256, 2) k_batch_df(const RunArgs32* __restrict__ sets,
+                                                     const CoefDF* __restrict__ coefs,
+                                                     const long long* __restrict__ base,
+                                                     const EpochEntry* __restrict__ entries, EpochDesc ep,
+                                                     int* __restrict__ counter, const float4* __restrict__ scd,
+                                                     TabDF tb) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float4* stab = reinterpret_cast<float4*>(smem);
+  __shared__ long long s_item[2];
+  __shared__ RunArgs32 s_ra[2];
+  __shared__ CoefDF s_cf[2];
+  for (int k = threadIdx.x; k <= tb.mask; k += blockDim.x) stab[k] = scd[k];
+  if (threadIdx.x == 0) pop_item(counter, ep, entries, sets, coefs, s_item, s_ra, s_cf, 0);
+  for (int it = 0;; ++it) {
+    __syncthreads();
+    const int slot = it & 1;
+    const long long item = s_item[slot];
+    if (item >= ep.tiles) break;
+    if (threadIdx.x == 0) pop_item(counter, ep, entries, sets, coefs, s_item, s_ra, s_cf, slot ^ 1);
+    long long t_idx;
+    const EpochEntry& en = find_entry(entries, ep, item, t_idx);
+    const RunArgs32& ra = s_ra[slot];
+    const long long i = t_idx * blockDim.x + threadIdx.x;
+    if (i < ra.n) run_traj_df<M, TAN, FAST>(ra, s_cf[slot], i, base[en.set] + en.step0_rel, en.nsteps, stab, tb);
   }
 }
 
@@ -117,6 +173,22 @@ int blocks_per_sm(int block, size_t smem) {
   return nb > 0 ? nb : 1;
 }
 
+template <int M, bool TAN, bool FAST>
+cudaError_t launch_epoch_df(int grid, int block, size_t smem, cudaStream_t st, const RunArgs32* sets,
+                            const CoefDF* coefs, const long long* base, const EpochEntry* entries, const EpochDesc& ep,
+                            int* counter, const float4* scd, const TabDF& tb) {
+  k_batch_df<M, TAN, FAST><<<grid, block, smem, st>>>(sets, coefs, base, entries, ep, counter, scd, tb);
+  return cudaGetLastError();
+}
+
+template <int M, bool TAN, bool FAST>
+int blocks_per_sm_df(int block, size_t smem) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_df<M, TAN, FAST>, block, smem) != cudaSuccess)
+    return 1;
+  return nb > 0 ? nb : 1;
+}
+
 }  // namespace
 
 }  // namespace arnold
@@ -125,19 +197,20 @@ using namespace arnold;
 
 struct arnold_batch {
   int n_sets = 0;
-  int scheme = 0, tangent = 1, device = 0;
+  int scheme = 0, precision = ARNOLD_FP32C, tangent = 1, device = 0;
   arnold_batch_tuning tune{};
   cudaStream_t stream = nullptr;
   std::vector<arnold_batch_set> sets;
   std::vector<arnold_ctx*> ctx;
   RunArgs32* d_sets = nullptr;
-  Coef32* d_coefs = nullptr;
+  void* d_coefs = nullptr;      // Coef32[n_sets] (FP32C) or CoefDF[n_sets] (DF64, DF64F)
   long long* d_base = nullptr;
   long long* d_steps = nullptr;
   EpochEntry* d_entries = nullptr;
   int* d_counters = nullptr;
   std::vector<EpochDesc> epochs;
-  const float2* scf = nullptr;
+  const float2* scf = nullptr;  // FP32 sincos table (FP32C)
+  const float4* scd = nullptr;  // double-float sincos table (DF64, DF64F)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   long long launches = 0;
@@ -153,16 +226,60 @@ int bstatus(cudaError_t e) {
   return ARNOLD_ECUDA;
 }
 
-cudaError_t launch_any(const arnold_batch* b, int grid, size_t smem, const EpochDesc& ep, int* counter,
-                       const Tab32& tb) {
-  const int M = b->scheme == ARNOLD_SCHEME_YOSHIDA6A ? 7 : (b->scheme == ARNOLD_SCHEME_TRIPLEJUMP6 ? 9 : 1);
+int kicks_of(int scheme) {
+  return scheme == ARNOLD_SCHEME_YOSHIDA6A ? 7 : (scheme == ARNOLD_SCHEME_TRIPLEJUMP6 ? 9 : 1);
+}
+
+bool is_df(int precision) { return precision == ARNOLD_DF64 || precision == ARNOLD_DF64F; }
+
+// Shared memory of one block: the mode's sincos table.
+size_t table_smem(int precision) {
+  if (is_df(precision)) {
+    TabDF tb;
+    df_tab(&tb);
+    return (size_t)(tb.mask + 1) * sizeof(float4);
+  }
+  Tab32 tb;
+  fp32_tab(&tb);
+  return (size_t)(tb.jmax + 1) * sizeof(float2);
+}
+
+cudaError_t launch_any(const arnold_batch* b, int grid, size_t smem, const EpochDesc& ep, int* counter) {
+  const int M = kicks_of(b->scheme);
   const bool T = b->tangent;
-  const int P = b->tune.traj_per_thread;
   const int B = b->tune.block_size;
+  if (is_df(b->precision)) {
+    TabDF tb;
+    df_tab(&tb);
+    const bool F = b->precision == ARNOLD_DF64F;
+    const CoefDF* cf = (const CoefDF*)b->d_coefs;
+#define ARNOLD_BATCH_LAUNCH_DF(MM, TT, FF)                                                                         \
+  if (M == MM && T == TT && F == FF)                                                                               \
+    return launch_epoch_df<MM, TT, FF>(grid, B, smem, b->stream, b->d_sets, cf, b->d_base, b->d_entries, ep, counter, \
+                                       b->scd, tb);
+    ARNOLD_BATCH_LAUNCH_DF(7, true, true)
+    ARNOLD_BATCH_LAUNCH_DF(7, false, true)
+    ARNOLD_BATCH_LAUNCH_DF(7, true, false)
+    ARNOLD_BATCH_LAUNCH_DF(7, false, false)
+    ARNOLD_BATCH_LAUNCH_DF(9, true, true)
+    ARNOLD_BATCH_LAUNCH_DF(9, false, true)
+    ARNOLD_BATCH_LAUNCH_DF(9, true, false)
+    ARNOLD_BATCH_LAUNCH_DF(9, false, false)
+    ARNOLD_BATCH_LAUNCH_DF(1, true, true)
+    ARNOLD_BATCH_LAUNCH_DF(1, false, true)
+    ARNOLD_BATCH_LAUNCH_DF(1, true, false)
+    ARNOLD_BATCH_LAUNCH_DF(1, false, false)
+#undef ARNOLD_BATCH_LAUNCH_DF
+    return cudaErrorInvalidValue;
+  }
+  Tab32 tb;
+  fp32_tab(&tb);
+  const int P = b->tune.traj_per_thread;
+  const Coef32* cf = (const Coef32*)b->d_coefs;
 #define ARNOLD_BATCH_LAUNCH(MM, TT, PP)                                                                            \
   if (M == MM && T == TT && P == PP)                                                                               \
-    return launch_epoch<MM, TT, PP>(grid, B, smem, b->stream, b->d_sets, b->d_coefs, b->d_base, b->d_entries, ep, \
-                                    counter, b->scf, tb);
+    return launch_epoch<MM, TT, PP>(grid, B, smem, b->stream, b->d_sets, cf, b->d_base, b->d_entries, ep, counter, \
+                                    b->scf, tb);
   ARNOLD_BATCH_LAUNCH(7, true, 1)
   ARNOLD_BATCH_LAUNCH(7, true, 2)
   ARNOLD_BATCH_LAUNCH(7, false, 1)
@@ -180,10 +297,29 @@ cudaError_t launch_any(const arnold_batch* b, int grid, size_t smem, const Epoch
 }
 
 int occupancy_any(const arnold_batch* b, size_t smem) {
-  const int M = b->scheme == ARNOLD_SCHEME_YOSHIDA6A ? 7 : (b->scheme == ARNOLD_SCHEME_TRIPLEJUMP6 ? 9 : 1);
+  const int M = kicks_of(b->scheme);
   const bool T = b->tangent;
-  const int P = b->tune.traj_per_thread;
   const int B = b->tune.block_size;
+  if (is_df(b->precision)) {
+    const bool F = b->precision == ARNOLD_DF64F;
+#define ARNOLD_BATCH_OCC_DF(MM, TT, FF) \
+  if (M == MM && T == TT && F == FF) return blocks_per_sm_df<MM, TT, FF>(B, smem);
+    ARNOLD_BATCH_OCC_DF(7, true, true)
+    ARNOLD_BATCH_OCC_DF(7, false, true)
+    ARNOLD_BATCH_OCC_DF(7, true, false)
+    ARNOLD_BATCH_OCC_DF(7, false, false)
+    ARNOLD_BATCH_OCC_DF(9, true, true)
+    ARNOLD_BATCH_OCC_DF(9, false, true)
+    ARNOLD_BATCH_OCC_DF(9, true, false)
+    ARNOLD_BATCH_OCC_DF(9, false, false)
+    ARNOLD_BATCH_OCC_DF(1, true, true)
+    ARNOLD_BATCH_OCC_DF(1, false, true)
+    ARNOLD_BATCH_OCC_DF(1, true, false)
+    ARNOLD_BATCH_OCC_DF(1, false, false)
+#undef ARNOLD_BATCH_OCC_DF
+    return 1;
+  }
+  const int P = b->tune.traj_per_thread;
 #define ARNOLD_BATCH_OCC(MM, TT, PP) \
   if (M == MM && T == TT && P == PP) return blocks_per_sm<MM, TT, PP>(B, smem);
   ARNOLD_BATCH_OCC(7, true, 1)
@@ -223,17 +359,19 @@ void arnold_batch_tuning_default(arnold_batch_tuning* t) {
   t->epoch_ms = 200;
 }
 
-int arnold_batch_create(const arnold_batch_set* sets, int n_sets, int scheme, int tangent,
+int arnold_batch_create(const arnold_batch_set* sets, int n_sets, int scheme, int precision, int tangent,
                         const arnold_batch_tuning* tuning, int device, void* cuda_stream, arnold_batch** out) {
   if (out) *out = nullptr;
   if (!out || !sets || n_sets <= 0 || n_sets > 4096 || scheme < 0 || scheme > 2 || (tangent != 0 && tangent != 1))
     return ARNOLD_EINVAL;
+  if (precision != ARNOLD_FP32C && precision != ARNOLD_DF64 && precision != ARNOLD_DF64F) return ARNOLD_EINVAL;
   arnold_batch_tuning tu;
   arnold_batch_tuning_default(&tu);
   if (tuning) tu = *tuning;
   if (tu.block_size < 32 || tu.block_size > 256 || tu.block_size % 32 || (tu.traj_per_thread != 1 && tu.traj_per_thread != 2) ||
       tu.renorm_every < 1 || tu.epoch_ms < 1)
     return ARNOLD_EINVAL;
+  if (is_df(precision) && tu.traj_per_thread != 1) return ARNOLD_EINVAL;
   for (int s = 0; s < n_sets; ++s) {
     const arnold_batch_set& q = sets[s];
     if (!(q.h != 0.0) || q.G <= 0 || q.G > (1 << 20) || q.n_steps < 0 || q.n_steps > (1LL << 40) ||
@@ -244,6 +382,7 @@ int arnold_batch_create(const arnold_batch_set* sets, int n_sets, int scheme, in
   if (!b) return ARNOLD_ENOMEM;
   b->n_sets = n_sets;
   b->scheme = scheme;
+  b->precision = precision;
   b->tangent = tangent;
   b->device = device;
   b->tune = tu;
@@ -252,6 +391,7 @@ int arnold_batch_create(const arnold_batch_set* sets, int n_sets, int scheme, in
   int st = ARNOLD_OK;
   std::vector<RunArgs32> hra(n_sets);
   std::vector<Coef32> hcf(n_sets);
+  std::vector<CoefDF> hcd(n_sets);
   std::vector<long long> hsteps(n_sets);
   for (int s = 0; s < n_sets && st == ARNOLD_OK; ++s) {
     arnold_params p;
@@ -259,24 +399,29 @@ int arnold_batch_create(const arnold_batch_set* sets, int n_sets, int scheme, in
     p.eps = sets[s].eps;
     p.h = sets[s].h;
     p.scheme = scheme;
-    p.precision = ARNOLD_FP32C;
+    p.precision = precision;
     p.tangent = tangent;
     p.renorm_every = tu.renorm_every;
     arnold_ctx* c = nullptr;
     st = arnold_create(&p, sets[s].G * sets[s].G, device, cuda_stream, &c);
     if (st) break;
     b->ctx.push_back(c);
-    st = ctx_run_args32(c, &hra[s], &hcf[s], &b->scf);
+    StepCoef sc;
+    st = ctx_run_args(c, &hra[s], &sc, &b->scf, &b->scd);
+    hcf[s] = coef32_from(sc);
+    hcd[s] = coef_df_from(sc);
     hsteps[s] = sets[s].n_steps;
   }
   cudaError_t e = cudaSuccess;
   if (st == ARNOLD_OK) {
+    const size_t cbytes = is_df(precision) ? sizeof(CoefDF) : sizeof(Coef32);
+    const void* hc = is_df(precision) ? (const void*)hcd.data() : (const void*)hcf.data();
     e = cudaMalloc(&b->d_sets, sizeof(RunArgs32) * n_sets);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_coefs, sizeof(Coef32) * n_sets);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_coefs, cbytes * n_sets);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_base, sizeof(long long) * n_sets);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_steps, sizeof(long long) * n_sets);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_sets, hra.data(), sizeof(RunArgs32) * n_sets, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(b->d_coefs, hcf.data(), sizeof(Coef32) * n_sets, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_coefs, hc, cbytes * n_sets, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_steps, hsteps.data(), sizeof(long long) * n_sets, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(b->d_base, 0, sizeof(long long) * n_sets);
     st = bstatus(e);
@@ -285,8 +430,9 @@ int arnold_batch_create(const arnold_batch_set* sets, int n_sets, int scheme, in
   std::vector<EpochEntry> entries;
   if (st == ARNOLD_OK) {
     const long long tile = (long long)tu.block_size * tu.traj_per_thread;
-    const int m = scheme == ARNOLD_SCHEME_YOSHIDA6A ? 7 : (scheme == ARNOLD_SCHEME_TRIPLEJUMP6 ? 9 : 1);
-    const double rate = 2.0e10 * 7.0 / m;                     // map-steps/s, FP32C estimate
+    // map-steps/s estimates of each mode (7 kicks per step), for the epoch length only
+    const double rate7 = precision == ARNOLD_FP32C ? 2.0e10 : (precision == ARNOLD_DF64F ? 1.1e10 : 7.0e9);
+    const double rate = rate7 * 7.0 / kicks_of(scheme);
     const double target = rate * tu.epoch_ms * 1e-3;          // map steps per epoch
     long long done = 0, max_steps = 0;
     for (auto& q : b->sets) max_steps = std::max(max_steps, (long long)q.n_steps);
@@ -364,9 +510,7 @@ int arnold_batch_run(arnold_batch* b) {
   cudaError_t e = cudaSetDevice(b->device);
   if (e != cudaSuccess) return bstatus(e);
   if (!b->exec) {
-    Tab32 tb;
-    fp32_tab(&tb);
-    const size_t smem = (size_t)(tb.jmax + 1) * sizeof(float2);
+    const size_t smem = table_smem(b->precision);
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
     const int grid = sms * occupancy_any(b, smem);
@@ -379,7 +523,7 @@ int arnold_batch_run(arnold_batch* b) {
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counters, 0, sizeof(int) * std::max<size_t>(1, b->epochs.size()), cs);
     for (size_t k = 0; k < b->epochs.size() && e == cudaSuccess; ++k)
-      e = launch_any(b, grid, smem, b->epochs[k], b->d_counters + k, tb);
+      e = launch_any(b, grid, smem, b->epochs[k], b->d_counters + k);
     if (e == cudaSuccess) {
       k_batch_advance<<<1, 256, 0, cs>>>(b->d_base, b->d_steps, b->n_sets);
       e = cudaGetLastError();

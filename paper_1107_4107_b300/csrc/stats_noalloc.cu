@@ -54,6 +54,14 @@ int to_status(cudaError_t e) {
   return ARNOLD_ECUDA;
 }
 
+// Makes `device` current for the call and gives the caller back its own
+// current device on every return path.
+struct DeviceScope {
+  int prev = -1;
+  explicit DeviceScope() { if (cudaGetDevice(&prev) != cudaSuccess) prev = -1; }
+  ~DeviceScope() { if (prev >= 0) cudaSetDevice(prev); }
+};
+
 }  // namespace
 
 }  // namespace arnold
@@ -68,6 +76,7 @@ extern "C" int arnold_stats_arrays_noalloc(int device, void* cuda_stream, int64_
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) return ARNOLD_EUNSUPPORTED;
   if (device >= ndev) return ARNOLD_EINVAL;
+  DeviceScope keep;
   cudaError_t e = cudaSetDevice(device);
   if (e != cudaSuccess) return to_status(e);
   StatsPartial* scratch = nullptr;

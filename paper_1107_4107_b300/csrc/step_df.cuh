@@ -12,9 +12,11 @@ namespace arnold {
 
 // Sincos table of the DF64 path: theta_j = 2 pi j / 2048, entry j holds
 // (sin hi, sin lo, cos hi, cos lo) rounded from long-double libm; the step
-// D = 2 pi / 2048 is split d1 (11 significant bits, so j d1 is exact for
-// |j| < 8192) + d2 + d3 (59 bits in all).  Angles are reduced every step, so
-// |x| <= 2 pi + h |q| and |j| < 8192 for h |q| < 9 per step.
+// D = 2 pi / 2048 is split d1 (11 significant bits, its last bit 2^-19) + d2 +
+// d3 (59 bits in all).  x.hi - j d1 is then exact for any |x| < 2^22 D: both
+// are multiples of min(ulp(x.hi), 2^-19) and their difference is below D.
+// Angles are reduced once they pass 12 rad at the end of a step, so within a
+// step |x| < 12 + h |q| (h |q| <= kDfMaxStepAngle, checked at renormalisation).
 struct TabDF {
   float inv_d, d1, d2, d3;
   int mask;          // 2047
@@ -239,10 +241,10 @@ __device__ __forceinline__ double potential_df(const T& t, const float4* tab, co
 namespace arnold {
 
 // End of a DF64 step: renormalise every pair, and once an angle passes 12 rad
-// remove whole turns from the angles (exactly, 2 pi as three floats).  With at
-// most 9 rad per step (checked at renormalisation, ERANGE otherwise) every
-// kick's argument stays below 21 rad, inside the table's exact index range
-// (|x| < 25).
+// remove whole turns from the angles (exactly, 2 pi as three floats: k c1 and
+// k c2 are exact for |k| < 64 turns, and angles stay below 12 + h |q| < 172 rad
+// while h |q| <= kDfMaxStepAngle, checked at renormalisation, ERANGE
+// otherwise).
 __device__ __forceinline__ void reduce_angle_df(Pair& x, int& lap, const TabDF& tb) {
   const float t = fmaf(x.hi, tb.inv2pi, 12582912.0f);
   const float kf = __fsub_rn(t, 12582912.0f);

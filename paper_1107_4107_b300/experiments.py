@@ -72,8 +72,9 @@ def diffusion_from_w(n: int = 32000, E: float = 15.0, sigma: float = 0.01, windo
     of width sigma and p_z from the energy; angles whose energy condition has no
     real p_z are redrawn (the cloud sits where |P|^2 = 2E, so the potential must
     be <= 0 there).  F of V over windows of window_T is accumulated between
-    consecutive snapshot times (time-averaged F).  With ckpt_path the state is
-    saved after every window and a rerun resumes from it."""
+    consecutive snapshot times (time-averaged F).  With ckpt_path the state, the
+    window count and the accumulated F are saved together after every window
+    (one file, replaced atomically) and a rerun resumes from it."""
     import torch
     h = paper_h() if h is None else h
     W = math.sqrt(E)
@@ -83,14 +84,10 @@ def diffusion_from_w(n: int = 32000, E: float = 15.0, sigma: float = 0.01, windo
     maps = []
     # F accumulates on the device between snapshots (no host round trip per window)
     acc = torch.zeros((n_cos, n_phi), dtype=torch.int64, device=f"cuda:{device}")
-    if ckpt_path and os.path.exists(ckpt_path):
-        blob = open(ckpt_path, "rb").read()
-        e.restore(blob[:-16])
-        done_windows = int(np.frombuffer(blob[-16:-8], dtype=np.int64)[0])
-        acc_path = ckpt_path + ".acc.npy"
-        if os.path.exists(acc_path):
-            acc.copy_(torch.from_numpy(np.load(acc_path).astype(np.int64)))
     bounds = [int(round(s * T / h / w_steps)) for s in snapshots_T]
+    if ckpt_path and os.path.exists(ckpt_path):
+        done_windows, acc_np = _load_fig4_ckpt(ckpt_path, e, bounds, (n_cos, n_phi))
+        acc.copy_(torch.from_numpy(acc_np))
     k = 0
     while k < len(bounds) and bounds[k] <= done_windows:
         k += 1
@@ -103,12 +100,43 @@ def diffusion_from_w(n: int = 32000, E: float = 15.0, sigma: float = 0.01, windo
             acc.zero_()
             k += 1
         if ckpt_path:
-            with open(ckpt_path, "wb") as f:
-                f.write(e.checkpoint() + np.array([done_windows, 0], dtype=np.int64).tobytes())
-            np.save(ckpt_path + ".acc.npy", acc.cpu().numpy().astype(np.uint64))
+            _save_fig4_ckpt(ckpt_path, e, done_windows, acc.cpu().numpy())
     e.sync()
     return {"maps": maps, "windows": done_windows, "n": n, "E": E, "window_steps": w_steps,
             "dE_max": float(e.indicator("dE_max").max())}
+
+
+def _save_fig4_ckpt(path: str, e: ArnoldEnsemble, done_windows: int, acc: np.ndarray) -> None:
+    """Ensemble checkpoint, window count and accumulated F in one file, written
+    to a private temporary and renamed over `path`: a crash leaves either the
+    previous checkpoint or the new one, never a mix."""
+    tmp = f"{path}.{os.getpid()}.tmp"
+    with open(tmp, "wb") as f:
+        np.savez(f, state=np.frombuffer(e.checkpoint(), dtype=np.uint8), done_windows=np.int64(done_windows),
+                 acc=acc.astype(np.int64))
+    os.replace(tmp, path)
+
+
+def _load_fig4_ckpt(path: str, e: ArnoldEnsemble, bounds, shape):
+    """Restore a Fig. 4 checkpoint into `e`; returns (done_windows, acc).  The
+    accumulated F must hold exactly the windows since the last snapshot
+    boundary, and have the run's F shape; anything else is an error."""
+    with np.load(path) as z:
+        if set(z.files) != {"state", "done_windows", "acc"}:
+            raise ValueError(f"{path}: not a Fig. 4 checkpoint")
+        done = int(z["done_windows"])
+        acc = z["acc"].astype(np.int64)
+        state = z["state"].tobytes()
+    if acc.shape != tuple(shape):
+        raise ValueError(f"{path}: F shape {acc.shape} != {tuple(shape)}")
+    last = max([b for b in bounds if b <= done], default=0)
+    n_acc = int(acc.sum())
+    if done > last and n_acc == 0:
+        raise ValueError(f"{path}: F holds no window since window {last}, but {done} windows are done")
+    if done == last and n_acc != 0:
+        raise ValueError(f"{path}: F is not empty at a snapshot boundary")
+    e.restore(state)
+    return done, acc
 
 
 def init_gaussian_valid(n: int, E: float, center, sigma: float, seed: int, **kw) -> ArnoldEnsemble:

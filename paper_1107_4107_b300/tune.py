@@ -6,7 +6,8 @@ events and keeps the fastest.  Results are cached per (GPU name, precision,
 scheme, tangent) in tune_cache.json next to this file.  The renormalisation
 interval only changes rounding of the FTLE (chi is independent of R) and the
 sampling interval of the energy error; candidates stay below R h lambda ~ 50,
-so the FP32 tangent cannot overflow between renormalisations.
+so the FP32 tangent cannot overflow between renormalisations.  The
+double-float modes run one trajectory per thread.
 """
 from __future__ import annotations
 
@@ -19,9 +20,13 @@ CANDIDATES = [{"block_size": b, "traj_per_thread": t, "renorm_every": r, "epoch_
               for b in (128, 256) for t in (1, 2) for r in (50, 100, 200)]
 
 
-def _key(scheme: str, tangent: bool, device: int) -> str:
+def candidates_for(precision: str):
+    return [c for c in CANDIDATES if precision == "fp32c" or c["traj_per_thread"] == 1]
+
+
+def _key(precision: str, scheme: str, tangent: bool, device: int) -> str:
     import torch
-    return f"{torch.cuda.get_device_name(device)}|fp32c|{scheme}|{int(tangent)}"
+    return f"{torch.cuda.get_device_name(device)}|{precision}|{scheme}|{int(tangent)}"
 
 
 def scaled(sets, g_div: int = 4, step_div: int = 200):
@@ -29,13 +34,13 @@ def scaled(sets, g_div: int = 4, step_div: int = 200):
 
 
 def tune_batch(sets, scheme: str = "yoshida6a", tangent: bool = True, use_cache: bool = True,
-               candidates=None, verbose: bool = False, device: int | None = None) -> dict:
-    """Best tuning for `sets` on `device` (default: torch's current device)."""
+               candidates=None, verbose: bool = False, device: int | None = None, precision: str = "fp32c") -> dict:
+    """Best tuning for `sets` in `precision` on `device` (default: torch's current device)."""
     import torch
     from .api import ArnoldBatch
     if device is None:
         device = torch.cuda.current_device()
-    key = _key(scheme, tangent, device)
+    key = _key(precision, scheme, tangent, device)
     cache = {}
     if use_cache and os.path.exists(CACHE):
         try:
@@ -47,9 +52,9 @@ def tune_batch(sets, scheme: str = "yoshida6a", tangent: bool = True, use_cache:
     sample = scaled(sets)
     results = []
     stream = torch.cuda.current_stream(device)
-    for cand in candidates or CANDIDATES:
+    for cand in candidates or candidates_for(precision):
         b = ArnoldBatch(sample, scheme=scheme, tangent=tangent, tuning=cand, device=device,
-                        stream=stream.cuda_stream)
+                        stream=stream.cuda_stream, precision=precision)
         b.init()
         b.run()          # captures the graph, warms up
         b.sync()

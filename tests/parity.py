@@ -55,3 +55,25 @@ def compare_state(ens, st, tangent=True):
         out["V"] = rel_err(ens.indicator("V"), st.velocity())
     out["dE_max"] = float(np.max(np.abs(ens.indicator("dE_max") - st.dE_max)))
     return out
+
+
+def cell_growth(st):
+    """Each cell's own tangent growth exp(chi t) over the run, from the oracle (at
+    least 1): the first-order amplification of an error made along the way."""
+    return np.maximum(1.0, np.exp(np.minimum(st.chi() * st.time(), 700.0)))
+
+
+def growth_scaled(got, ref, growth, bound, power=1):
+    """Per-cell parity bar: |got - ref| / (1 + |ref|) (worst component of a
+    [k][n] quantity) <= bound * growth^power, for every cell.  power = 1 for the
+    state, V and the FTLE (first-order propagation of rounding); power = 2 for
+    the tangent components, which are first derivatives of the flow and so
+    carry the second-order sensitivity of the state errors.  Returns
+    (ok, worst err / bar)."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    err = np.abs(got - ref) / (1.0 + np.abs(ref))
+    if err.ndim == 2:
+        err = np.max(err, axis=0)
+    bar = bound * np.asarray(growth, dtype=np.float64) ** power
+    return bool(np.all(err <= bar)), float(np.max(err / bar))

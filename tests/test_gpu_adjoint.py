@@ -145,6 +145,23 @@ def test_autograd_function_variance_loss():
     assert abs(eps.grad.item() - oe) <= 1e-9 * abs(oe)
 
 
+def test_autograd_function_with_float_parameters():
+    """h and eps given as plain floats: only X0 and P0 get gradients, and the
+    backward pass accepts that (autograd takes no gradient for a non-tensor)."""
+    torch = pytest.importorskip("torch")
+    from paper_1107_4107_b300.api import arnold_map
+    n, N = 64, 150
+    X, P = inputs.box(n, seed=4)
+    Xt = torch.tensor(X, device="cuda", requires_grad=True)
+    Pt = torch.tensor(P, device="cuda", requires_grad=True)
+    XN, PN = arnold_map(Xt, Pt, H, 1.0, N)
+    loss = PN.var(dim=1, unbiased=False).mean()
+    loss.backward()
+    ox, op, _, _, _, _ = oracle.gradient(oracle.Params(h=H), X, P, N)
+    assert _rel(Xt.grad.cpu().numpy(), ox) < 1e-9
+    assert _rel(Pt.grad.cpu().numpy(), op) < 1e-9
+
+
 def test_sharded_variance_gradient_equals_whole_ensemble():
     """Two shards of one ensemble, each with its own context and CUDA adjoint, run
     the sharded variance-loss gradient (loss partials exchanged before the reverse

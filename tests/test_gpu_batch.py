@@ -1,6 +1,8 @@
 """Batched persistent launch (many (K, eps) sets of uneven sizes and step counts,
-one CUDA-graph launch, FP32C): every set must be bit-identical to a single
-FP32C ensemble with the same parameters, for any tuning, across repeated runs."""
+one CUDA-graph launch, FP32C or double-float): every set must be bit-identical
+to a single ensemble of the same precision with the same parameters, for any
+tuning, across repeated runs.  The single ensembles are themselves held to the
+oracle by the per-precision parity tests."""
 import numpy as np
 import pytest
 
@@ -19,19 +21,27 @@ SETS = [
 KINDS = ("X", "P", "dX", "tangent", "chi", "dE_max", "logsum")
 
 
-def _single(q, steps_list, R):
+def _single(q, steps_list, R, precision):
     from paper_1107_4107_b300.api import ArnoldEnsemble
-    e = ArnoldEnsemble(q["G"] ** 2, eps=q["eps"], h=q["h"], precision="fp32c", renorm_every=R)
+    e = ArnoldEnsemble(q["G"] ** 2, eps=q["eps"], h=q["h"], precision=precision, renorm_every=R)
     e.init_grid(q["G"], q["E"], seed=q["seed"])
     for s in steps_list:
         e.iterate(s)
-    return {k: e.indicator(k) for k in KINDS}
+    out = {k: e.indicator(k) for k in KINDS}
+    e.sync()
+    return out
 
 
-@pytest.mark.parametrize("tuning", [None, {"block_size": 128, "traj_per_thread": 2, "renorm_every": 50, "epoch_ms": 5}])
-def test_batch_bitwise_equals_single_ensembles(tuning):
+@pytest.mark.parametrize("precision,tuning", [
+    ("fp32c", None),
+    ("fp32c", {"block_size": 128, "traj_per_thread": 2, "renorm_every": 50, "epoch_ms": 5}),
+    ("df64f", None),
+    ("df64f", {"block_size": 128, "traj_per_thread": 1, "renorm_every": 50, "epoch_ms": 5}),
+    ("df64", {"block_size": 64, "traj_per_thread": 1, "renorm_every": 100, "epoch_ms": 5}),
+])
+def test_batch_bitwise_equals_single_ensembles(precision, tuning):
     from paper_1107_4107_b300.api import ArnoldBatch
-    b = ArnoldBatch(SETS, tuning=tuning)
+    b = ArnoldBatch(SETS, tuning=tuning, precision=precision)
     R = b.tuning["renorm_every"]
     b.init()
     b.run()
@@ -41,9 +51,21 @@ def test_batch_bitwise_equals_single_ensembles(tuning):
     assert info["map_steps_per_run"] == sum(q["G"] ** 2 * q["n_steps"] for q in SETS)
     assert info["epochs"] >= 1
     for k, q in enumerate(SETS):
-        ref = _single(q, [q["n_steps"], q["n_steps"]], R)
+        ref = _single(q, [q["n_steps"], q["n_steps"]], R, precision)
         for kind in KINDS:
             assert np.array_equal(b.indicator(k, kind), ref[kind]), (k, kind)
+
+
+def test_batch_double_float_rejects_two_per_thread():
+    from paper_1107_4107_b300._lib import ArnoldError, EINVAL
+    from paper_1107_4107_b300.api import ArnoldBatch
+    with pytest.raises(ArnoldError) as ex:
+        ArnoldBatch(SETS[:2], precision="df64f", tuning={"block_size": 128, "traj_per_thread": 2,
+                                                         "renorm_every": 100, "epoch_ms": 5})
+    assert ex.value.status == EINVAL
+    with pytest.raises(ArnoldError) as ex:
+        ArnoldBatch(SETS[:2], precision="fp64")
+    assert ex.value.status == EINVAL
 
 
 def test_batch_plan_for_the_batched_scan_config():
@@ -61,12 +83,13 @@ def test_batch_plan_for_the_batched_scan_config():
         assert s["n"] == sets[k]["G"] ** 2
 
 
-def test_autotuner_picks_and_caches(tmp_path, monkeypatch):
+@pytest.mark.parametrize("precision", ["fp32c", "df64f"])
+def test_autotuner_picks_and_caches(tmp_path, monkeypatch, precision):
     from paper_1107_4107_b300 import tune
     monkeypatch.setattr(tune, "CACHE", str(tmp_path / "cache.json"))
     cands = [{"block_size": 128, "traj_per_thread": 1, "renorm_every": 100, "epoch_ms": 50},
              {"block_size": 256, "traj_per_thread": 1, "renorm_every": 100, "epoch_ms": 50}]
-    best = tune.tune_batch(SETS, candidates=cands)
+    best = tune.tune_batch(SETS, candidates=cands, precision=precision)
     assert best in cands
-    assert tune.tune_batch(SETS, candidates=cands) == best      # from the cache
+    assert tune.tune_batch(SETS, candidates=cands, precision=precision) == best      # from the cache
     assert (tmp_path / "cache.json").exists()

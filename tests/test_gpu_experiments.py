@@ -47,3 +47,61 @@ def test_scan_agreement_runs_all_modes_from_the_same_ics():
     for r in rows[1:]:
         assert r["class_agreement"] >= 0.99 and r["hist_l1"] <= 1e-2
     assert all(r["map_steps_per_s"] > 0 for r in rows)
+
+
+def test_diffusion_resume_rejects_an_inconsistent_checkpoint(tmp_path):
+    """A checkpoint whose accumulated F does not hold the windows since the last
+    snapshot boundary of the resumed schedule is refused, not silently used."""
+    from paper_1107_4107_b300.experiments import diffusion_from_w
+    kw = dict(n=1000, E=15.0, window_T=1.0, n_cos=8, n_phi=8, precision="fp32c")
+    ck = str(tmp_path / "run.ckpt")
+    diffusion_from_w(**kw, snapshots_T=(2.0,), ckpt_path=ck)     # stops at a boundary: F empty
+    with pytest.raises(ValueError):
+        diffusion_from_w(**kw, snapshots_T=(3.0,), ckpt_path=ck)   # would need windows 1-2 in F
+    with open(ck, "r+b") as f:                                     # a truncated file
+        f.truncate(100)
+    with pytest.raises(Exception):
+        diffusion_from_w(**kw, snapshots_T=(2.0, 4.0), ckpt_path=ck)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "df64f"])
+def test_fig4_windows_match_oracle(precision):
+    """Sec. IV, Fig. 4 on a small cloud: 500 trajectories Gaussian about W at
+    E = 15, p_z from the energy with redraws, three windows of 1 T.  The kept
+    initial conditions are exactly the draws the oracle's energy condition
+    keeps (in order), and each time-averaged F of the runner equals the
+    oracle's histogram of its own window velocities, up to bin-edge moves."""
+    import oracle
+    from paper_1107_4107_b300 import inputs
+    from paper_1107_4107_b300.experiments import diffusion_from_w, init_gaussian_valid
+    from parity import angle_dist, rel_err
+    n, E, sigma, seed = 500, 15.0, 0.01, 0
+    W = math.sqrt(E)
+    h = 0.02 * math.pi
+    w_steps = 100                                   # 1 T
+    cand = max(2 * n, 1024)
+    X, Pxy = inputs.gaussian_velocities(cand, (W, W), sigma, seed)
+    P = np.zeros((3, cand))
+    P[:2] = Pxy
+    Po = oracle.pz_from_energy(E, 1.0, X, P)
+    ok = np.isfinite(Po[2])
+    assert 0.05 < ok.mean() < 0.95                  # the redraw really drops draws here
+    Xk, Pk = X[:, ok][:, :n], Po[:, ok][:, :n]
+    e = init_gaussian_valid(n, E, (W, W), sigma, seed, precision=precision, window=w_steps)
+    assert np.max(angle_dist(e.indicator("X"), Xk)) < 1e-13
+    assert rel_err(e.indicator("P"), Pk) < (1e-14 if precision == "fp64" else 1e-13)
+    e.close()
+    n_cos, n_phi = 16, 32
+    run = diffusion_from_w(n=n, E=E, sigma=sigma, window_T=1.0, snapshots_T=(1.0, 3.0), n_cos=n_cos, n_phi=n_phi,
+                           precision=precision, seed=seed)
+    st = oracle.State(Xk, Pk, oracle.Params(h=h, window=w_steps), tangent=False)
+    F = []
+    for _ in range(3):
+        st.advance(w_steps)
+        F.append(oracle.velocity_histogram(st.velocity(), n_cos, n_phi))
+    refs = [F[0], F[1] + F[2]]
+    allowed = 2 if precision == "fp64" else 6
+    for m, ref in zip(run["maps"], refs):
+        got = m["counts"].astype(np.int64)
+        assert got.sum() == ref.sum()
+        assert np.abs(got - ref).sum() <= 2 * allowed, (m["t_T"], np.abs(got - ref).sum())

@@ -7,8 +7,9 @@ table method vs libm, ~1 ulp) and the rotated coordinates used on the GPU
 |gpu - oracle| / (1 + |oracle|) on the unwrapped displacement, the momenta,
 the tangent vector and the indicators, at several step counts.  Chaotic
 trajectories amplify rounding like exp(lambda t), so all cells are compared
-over 100 steps (t = 6.3) and low-growth cells (tangent growth below e^5) up
-to 1000 steps from identical inputs.
+over 100 steps (t = 6.3) at 1e-12, and over 1000 steps from identical inputs
+at 1e-12 times each cell's own tangent growth exp(chi t) (its square for the
+tangent components).
 """
 import math
 
@@ -122,12 +123,16 @@ def test_grid_parity_all_cells(torch_cuda, E):
 
 
 @pytest.mark.parametrize("lo,hi", [((10.0, 4.0, 25.0), (11.0, 5.0, 26.0)), ((4.0, 1.0, 6.0), (5.0, 2.0, 7.0))])
-def test_long_horizon_parity_low_growth_cells(torch_cuda, lo, hi):
-    """1000 steps from identical seeded inputs (E ~ 390 and E ~ 30): on cells whose
-    tangent grew less than e^5 the state, FTLE and V agree to 1e-12.  The tangent
-    vector itself depends on second derivatives of the flow, which grow like t^2
-    on regular orbits: a rounding random walk of ~1e-16 * sqrt(7000 kicks) ~ 1e-14
-    times t^2 ~ 4e3 at t = 63 gives ~4e-11, so its components are held to 1e-10."""
+def test_long_horizon_parity_growth_scaled(torch_cuda, lo, hi):
+    """1000 steps from identical seeded inputs (E ~ 390 and E ~ 30), every cell
+    held to the 1e-12 bar times its own tangent growth G = exp(chi t) from the
+    oracle: an error made at step s reaches step N multiplied by at most the
+    flow's stretching, which the tangent measures.  State, V and FTLE: 1e-12 G.
+    The tangent components are first derivatives of the flow, so a state error
+    enters them through the second derivatives, whose growth is the square of
+    the first's (t^2 on a regular orbit's shear): 1e-12 G^2.  Classes must agree
+    wherever chi is farther from the threshold than its bar."""
+    from parity import cell_growth, growth_scaled
     n = 1024
     X, P = inputs.box(n, lo=lo, hi=hi, seed=13)
     prm = oracle_params(R=100)
@@ -135,13 +140,18 @@ def test_long_horizon_parity_low_growth_cells(torch_cuda, lo, hi):
     ens = _ens(n)
     ens.set_state(X, P)
     ens.iterate(1000)
-    low = st.chi() * st.time() < 5.0
-    assert low.mean() > 0.3
-    for kind, ref in (("dX", st.unwrapped_displacement()), ("P", st.P), ("V", st.velocity())):
-        assert rel_err(ens.indicator(kind)[:, low], ref[:, low]) < TOL, kind
-    assert rel_err(ens.indicator("chi")[low], st.chi()[low]) < TOL
-    assert rel_err(ens.indicator("tangent")[:, low], st.W[:, low]) < 1e-10
-    assert np.array_equal(ens.indicator("class")[low], st.classify()[low])
+    g = cell_growth(st)
+    report = {}
+    for kind, ref, power in (("dX", st.unwrapped_displacement(), 1), ("P", st.P, 1), ("V", st.velocity(), 1),
+                             ("chi", st.chi(), 1), ("tangent", st.W, 2)):
+        ok, worst = growth_scaled(ens.indicator(kind), ref, g, TOL, power)
+        report[kind] = worst
+        assert ok, (kind, worst)
+    print("worst err / bar:", report, "growth median", float(np.median(g)), "max", float(g.max()))
+    chi_o = st.chi()
+    thr = oracle.chaos_threshold(st.time())
+    clear = np.abs(chi_o - thr) > TOL * g * (1.0 + np.abs(chi_o))
+    assert np.array_equal(ens.indicator("class")[clear], st.classify()[clear])
 
 
 def test_window_velocity_parity(torch_cuda):
@@ -272,8 +282,9 @@ def test_oracle_scale_scan_128x128_1e4_steps(torch_cuda, E):
     """The whole oracle-scale scan (128 x 128 grid, 16,384 trajectories, 1e4 steps with
     tangent) against the oracle run of the same configuration.  Past the Lyapunov time
     chaotic trajectories decorrelate, so the bar is the scan-level one: class agreement
-    >= 99.5 %, chi-histogram L1 <= 1e-2; low-growth cells (chi t < 5) also agree on the
-    log sum of the tangent to 1e-6."""
+    >= 99.5 %, chi-histogram L1 <= 1e-2; every cell also agrees on the log sum of the
+    tangent to 1e-10 times its own tangent growth exp(chi t) (the first-order
+    propagation bound, with the 1e4-step sum of roundings)."""
     import os
     G = 128
     ens = _ens(G * G)
@@ -283,13 +294,14 @@ def test_oracle_scale_scan_128x128_1e4_steps(torch_cuda, E):
     cls, chi = ens.indicator("class"), ens.indicator("chi")
     agree = float(np.mean(cls == st.classify()))
     l1 = _hist_l1(chi, st.chi())
-    low = st.chi() * st.time() < 5.0
-    dlog = float(np.max(np.abs(chi[low] - st.chi()[low]))) * st.time()
+    from parity import cell_growth
+    g = cell_growth(st)
+    ratio = float(np.max(np.abs(chi - st.chi()) * st.time() / (1e-10 * g)))
     print(f"E={E}: agreement {agree:.5f}, L1 {l1:.2e}, chaotic {cls.mean():.4f}, "
-          f"low-growth cells {low.mean():.3f} with max |d log sum| {dlog:.2e}")
+          f"max |d log sum| / (1e-10 exp(chi t)) = {ratio:.2e}")
     assert agree >= 0.995
     assert l1 <= 1e-2
-    assert dlog < 1e-6
+    assert ratio <= 1.0
 
 
 def test_oracle_scale_scan_paper_moderate_E15(torch_cuda):

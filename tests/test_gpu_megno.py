@@ -5,8 +5,8 @@ Bars.  MEGNO is a weighted sum of the renormalisation logs; by summation by
 parts Y_m = 2 L_m - (2/m) sum_{k<m} L_k (L_k the log sum after k
 renormalisations), so |dY| <= 4 max_k |dL_k| and |d<Y>| likewise.  FP64: the
 log sums agree to rounding (the FTLE bar, 1e-12 relative) over 100 steps on
-all cells; on low-growth cells to 1000 steps the tangent is held to 1e-10, so
-MEGNO to 4e-10.  FP32C carries the tangent in FP32, whose log-sum error grows
+all cells; to 1000 steps every cell's tangent is held to 1e-12 G^2 (G its own
+tangent growth exp(chi t)), so MEGNO to 4e-12 G^2.  FP32C carries the tangent in FP32, whose log-sum error grows
 about linearly in the step count (bar below); DF64 carries it in double-float
 (~48 bits), held to the FP64 bars x 2^5.  The tests check the
 summation-by-parts bound itself against both sides' recorded log-sum
@@ -58,16 +58,20 @@ def test_megno_fp64_all_cells(n):
         assert _megno_err(ens, st) < 1e-12, (st.steps, _megno_err(ens, st))
 
 
-def test_megno_fp64_low_growth_cells_long():
+def test_megno_fp64_long_growth_scaled():
+    """1000 steps, every cell: 4 x the FP64 tangent bar 1e-12 G^2 (G = exp(chi t)
+    from the oracle), by the summation-by-parts bound."""
+    from parity import cell_growth, growth_scaled
     X, P = inputs.box(512, lo=(-4.0, -4.0, 20.0), hi=(4.0, 4.0, 21.0), seed=22)
     prm = oracle_params(R=10)
     st = oracle.State(X, P, prm).advance(1000, threads=4)
     ens = _ens(512, renorm_every=10)
     ens.set_state(X, P)
     ens.iterate(1000)
-    low = st.chi() * st.time() < 5.0
-    assert low.mean() > 0.3
-    assert _megno_err(ens, st, low) < 4e-10
+    g = cell_growth(st)
+    for kind, ref in (("megno", st.megno_mean()), ("megno_y", st.megno_y())):
+        ok, worst = growth_scaled(ens.indicator(kind), ref, g, 4e-12, 2)
+        assert ok, (kind, worst)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32c", "df64", "df64f"])
@@ -100,11 +104,11 @@ LOG_BAR_PER_STEP = 2.0 * 15.0 * 2.0 ** -24
 @pytest.mark.parametrize("n", [33, 700])
 def test_megno_pair_modes_vs_oracle(precision, n):
     """Ragged sizes (padding slots repeat the last trajectory and must not add to its
-    sums a second time); low-growth cells over 1000 steps.  Both sides' log sums are
+    sums a second time); every cell over 1000 steps.  Both sides' log sums are
     read after every renormalisation, so the summation-by-parts bound
     |dY|, |d<Y>| <= 4 max_k |dL_k| is checked exactly, and the log sums against the
-    FP32-tangent bar above (FP32C) or the FP64 low-growth tangent bar 1e-10 x 2^5
-    (DF64)."""
+    FP32-tangent bar above (FP32C), the FP64 tangent bar 1e-12 G^2 x 2^5 (DF64) or
+    the DF64F FTLE bar times t, each times the cell's own tangent growth G."""
     X, P = inputs.box(n, lo=(-4.0, -4.0, 20.0), hi=(4.0, 4.0, 21.0), seed=24)
     R, m = 20, 50
     st = oracle.State(X, P, oracle_params(R=R))
@@ -115,17 +119,18 @@ def test_megno_pair_modes_vs_oracle(precision, n):
         st.advance(R, threads=4)
         ens.iterate(R)
         dL = np.maximum(dL, np.abs(ens.indicator("logsum") - st.logsum))
-    low = st.chi() * st.time() < 5.0
-    assert low.sum() >= min(n, 10) // 2
+    from parity import cell_growth
+    g = cell_growth(st)
     for kind, ref in (("megno", st.megno_mean()), ("megno_y", st.megno_y())):
         d = np.abs(ens.indicator(kind) - ref)
         assert np.all(d <= 4.0 * dL + 1e-12 * (1.0 + np.abs(ref))), kind
-    worst = float(dL[low].max())
-    # FP32C: the FP32-tangent bar; DF64: the FP64 low-growth bar x 2^5; DF64F: its
-    # 1000-step FTLE bar times t
-    bar = {"fp32c": LOG_BAR_PER_STEP * R * m, "df64": 32 * 1e-10, "df64f": 1e-8 * R * m * 0.02 * math.pi}[precision]
-    print(f"{precision} n={n}: max |d log sum| on low-growth cells = {worst:.2e} (bar {bar:.2e})")
-    assert worst < bar, worst
+    # per cell, times its own tangent growth G: FP32C the FP32-tangent bar; DF64 the
+    # FP64 tangent bar 1e-12 G^2 x 2^5; DF64F its 1000-step FTLE bar times t
+    bar = {"fp32c": LOG_BAR_PER_STEP * R * m * g, "df64": 32 * 1e-12 * g ** 2,
+           "df64f": 1e-8 * R * m * 0.02 * math.pi * g}[precision]
+    worst = float(np.max(dL / bar))
+    print(f"{precision} n={n}: max |d log sum| / bar = {worst:.2e}")
+    assert worst < 1.0, worst
     # the last trajectory (the one padding slots repeat) holds the same bound
     ref_last = st.megno_mean()[-1]
     assert abs(ens.indicator("megno")[-1] - ref_last) <= 4.0 * dL[-1] + 1e-12 * (1.0 + abs(ref_last))

@@ -83,3 +83,42 @@ def test_filtered_histogram_counts_only_tracked_trajectories():
     phi = np.mod(np.arctan2(V[1], V[0]), TWO_PI)
     inside = (c >= patch[0]) & (c <= patch[1]) & (phi >= patch[2]) & (phi <= patch[3])
     assert H.sum() == int(np.sum(inside & (left == 0)))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "df64f"])
+def test_tracked_run_resumes_bitwise_from_checkpoint(precision):
+    """A checkpoint taken with area tracking on carries the flags: a fresh
+    context tracking the same patch, restored and continued, ends with the
+    uninterrupted run's flags, state and filtered F; a context that does not
+    track (or tracks another patch) is refused."""
+    from paper_1107_4107_b300._lib import ArnoldError, EINVAL
+    n, E = 4000, 15.0
+    patch = (0.2, 0.45, 0.6, 1.1)
+
+    def fresh():
+        e = _ens(n, tangent=False, renorm_every=5, precision=precision)
+        e.init_sphere(E, seed=12, cos_range=patch[:2], phi_range=patch[2:])
+        e.track_patch(*patch)
+        return e
+
+    ref = fresh()
+    ref.iterate(300)
+    a = fresh()
+    a.iterate(120)
+    blob = a.checkpoint()
+    assert 0 < int(a.indicator("left").sum()) < n    # some flags are set when the checkpoint is taken
+    b = _ens(n, tangent=False, renorm_every=5, precision=precision)
+    b.track_patch(*patch)
+    b.restore(blob)
+    b.iterate(180)
+    assert np.array_equal(b.indicator("left"), ref.indicator("left"))
+    assert np.array_equal(b.indicator("P"), ref.indicator("P"))
+    assert np.array_equal(b.velocity_histogram(10, 10, patch=patch, filtered=True),
+                          ref.velocity_histogram(10, 10, patch=patch, filtered=True))
+    for other in (None, (0.2, 0.45, 0.6, 1.2)):
+        c = _ens(n, tangent=False, renorm_every=5, precision=precision)
+        if other:
+            c.track_patch(*other)
+        with pytest.raises(ArnoldError) as ex:
+            c.restore(blob)
+        assert ex.value.status == EINVAL

@@ -48,7 +48,9 @@ def test_noalloc_stats_match_regular_entry_point_twice():
     ens = ArnoldEnsemble(8)
     for n, seed, t in ((1_000_003, 41, 628.3185307179587), (70_001, 42, 6283.185307179586)):
         chi, dE, P = _arrays(torch, n, seed)
+        before = torch.cuda.current_device()
         got = _noalloc(torch, chi, dE, P, t)
+        assert torch.cuda.current_device() == before     # the caller's device is left as it was
         ref = ens.stats_arrays(chi, dE, P, t)
         assert got["n"] == ref["n"] == n
         assert np.array_equal(got["hist"], ref["hist"])
