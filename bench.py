@@ -12,8 +12,13 @@ statistics, as a scan does at each output point.  The metric is map-steps/s
 (one map step = one composite step of one trajectory, tangent included).
 The state (~0.9 GB) is far larger than L2, so no flush is needed.
 
-Under torchrun (N > 1) each rank scans its own 2048 x 2048 grid (seed =
-rank): independent problems, no collective on the data path, weak scaling.
+Under torchrun (N > 1) the ranks share the one 2048 x 2048 scan: rank r takes a
+contiguous band of grid rows (the single-GPU scan's own initial conditions),
+and every bench step merges the ranks' ensemble statistics over the process
+group in rank order, the scan's one exchange (strong scaling).  --shard
+independent instead gives each rank its own 2048 x 2048 grid (seed = rank, no
+collective on the data path, weak scaling).  The single-GPU legs (precision
+modes, adjoint, batch, long horizon) run at N = 1 only.
 --impl reference times the FP64 CPU oracle on the host cores instead.
 """
 from __future__ import annotations
@@ -61,6 +66,7 @@ FP64_ISSUED_PER_STEP_NCU = 8018
 # the issue peak: one warp instruction per clock per SM sub-partition).
 NOMINAL_FP64_INSTR_PER_S = 1.25e12 / 2
 NOMINAL_FP32_INSTR_PER_S = 148 * 128 * 2032e6
+SM_MAX_MHZ = 2032.0
 
 
 def parse():
@@ -72,6 +78,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp32c", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the adjoint and batch legs")
+    ap.add_argument("--shard", default="band", choices=["band", "independent"],
+                    help="N > 1: bands of one scan with a statistics merge (band) or one scan per rank")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="scale of the batched config's step counts (1 = as configured)")
@@ -184,7 +192,8 @@ def run_reference(args, rank: int):
     v = statistics.mean(r["value"] for r in vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "map-steps/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak" if args.shard == "independent" else "strong",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config(args),
             "cpu_baseline": {"value": v, "unit": "map-steps/s", "cores": vals[0]["cores"], "kind": "oracle",
                              "sample": vals[0]["sample"] + f"; mean of {args.steps} samples"},
@@ -197,11 +206,36 @@ def config(args):
                         "(eps_eff=0.005), eps=1, h=0.01T, Yoshida-6A, tangent renormalised every 100 steps, "
                         f"1e6-step scan timed in chunks of {args.chunk} steps",
             "grid": G, "n_traj": G * G, "E": E, "eps": EPS, "h": H, "scheme": "yoshida6a", "precision": "fp64",
-            "steps_per_bench_step": args.chunk, "scan_horizon": HORIZON, "global_batch": G * G * args.gpus,
-            "parallelism": f"independent scans x{args.gpus}", "l2": "state 0.9 GB > 126 MB L2 (no flush needed)"}
+            "steps_per_bench_step": args.chunk, "scan_horizon": HORIZON,
+            "global_batch": G * G * (args.gpus if args.shard == "independent" else 1),
+            "parallelism": (f"independent scans x{args.gpus}" if args.shard == "independent" else
+                            f"one scan in {args.gpus} row bands, statistics merged over the ranks every step"),
+            "l2": "state 0.9 GB > 126 MB L2 (no flush needed)"}
 
 
 # ------------------------------------------------------------------ ours ---
+def rank_workload(world: int, rank: int, mode: str, grid: int = G):
+    """(row0, rows, seed) of this rank's part of the scan: a band of the one
+    grid x grid scan (mode "band"), or a whole grid of its own ("independent")."""
+    from paper_1107_4107_b300 import shard
+    if mode == "band":
+        row0, rows = shard.row_band(grid, rank, world)
+        return row0, rows, 0
+    return 0, grid, rank
+
+
+def bench_step(ens, chunk: int, outs: dict, gather=None):
+    """One bench step of a rank: advance its trajectories `chunk` composite steps,
+    write the indicator fields into `outs` (chi, class, V, dE_max), reduce its
+    ensemble statistics and, for a banded scan, merge them over the ranks
+    (gather).  Returns the statistics of the whole scan."""
+    ens.iterate(chunk)
+    for kind in ("chi", "class", "V", "dE_max"):
+        ens.indicator(kind, out=outs[kind])
+    s = ens.stats()
+    return gather(s) if gather else s
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -219,40 +253,70 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     stream = torch.cuda.current_stream()
-    n = G * G
+    mode = args.shard
+    row0, rows, seed = rank_workload(world, rank, mode)
+    n = rows * G
+    gather = None
+    if world > 1 and mode == "band":
+        from paper_1107_4107_b300 import shard
+        gather = shard.gather_stats
+    extras = world == 1 and not args.no_extras
 
     def barrier():
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
 
-    # peaks of this GPU, measured live (FP64 pipe, FP32 pipe)
-    dfma = probe_peak("dfma", local)
-    ffma = probe_peak("ffma", local)
+    # peaks of this GPU, measured live (FP64 pipe, FP32 pipe), with the SM clock
+    # sampled during each probe: lane-operations per SM per clock, and the rate
+    # that gives at the maximum SM clock
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    probes = {}
+    for kind in ("dfma", "ffma"):
+        with ClockSampler(local) as pc:
+            rate = probe_peak(kind, local)
+        c = pc.summary()
+        mhz = c["sm_mhz"] or SM_MAX_MHZ
+        probes[kind] = {"ops_per_s": rate, "sm_mhz": c["sm_mhz"], "clock_samples": c["samples"],
+                        "ops_per_sm_per_clock": rate / (sms * mhz * 1e6),
+                        "ops_per_s_at_max_clock": rate * SM_MAX_MHZ / mhz}
+    dfma = probes["dfma"]["ops_per_s"]
+    ffma = probes["ffma"]["ops_per_s"]
+    dfma_peak = probes["dfma"]["ops_per_s_at_max_clock"]
 
     ens = ArnoldEnsemble(n, precision="fp64", device=local, stream=stream.cuda_stream)
-    ens.init_grid(G, E, seed=rank)
-    chi = torch.empty(n, device="cuda", dtype=torch.float64)
-    V = torch.empty((3, n), device="cuda", dtype=torch.float64)
-    dEm = torch.empty(n, device="cuda", dtype=torch.float64)
-    cls = torch.empty(n, device="cuda", dtype=torch.uint8)
+    ens.init_grid(G, E, seed=seed, row0=row0)
+    outs = {"chi": torch.empty(n, device="cuda", dtype=torch.float64),
+            "V": torch.empty((3, n), device="cuda", dtype=torch.float64),
+            "dE_max": torch.empty(n, device="cuda", dtype=torch.float64),
+            "class": torch.empty(n, device="cuda", dtype=torch.uint8)}
 
     it_ms = []
 
+    class _Timed:
+        """The ensemble with its iterate bracketed by CUDA events (the kernel time
+        of the dominant launch, for the roofline)."""
+        def __init__(self, e):
+            self.e = e
+            self.timed = False
+
+        def iterate(self, k):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            self.e.iterate(k)
+            e1.record(stream)
+            if self.timed:
+                it_ms.append((e0, e1))
+
+        def __getattr__(self, name):
+            return getattr(self.e, name)
+
+    tens = _Timed(ens)
+
     def one_step(timed=False):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ens.iterate(args.chunk)
-        e1.record(stream)
-        ens.indicator("chi", out=chi)
-        ens.indicator("class", out=cls)
-        ens.indicator("V", out=V)
-        ens.indicator("dE_max", out=dEm)
-        s = ens.stats()
-        if timed:
-            it_ms.append((e0, e1))
-        return s
+        tens.timed = timed
+        return bench_step(tens, args.chunk, outs, gather)
 
     lw = ens.launches
     ens.iterate(args.chunk)
@@ -275,7 +339,7 @@ def main():
         tt = torch.tensor([ms], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms = float(tt.item())
-    total_steps = n * args.chunk * args.steps * world
+    total_steps = G * G * args.chunk * args.steps * (world if mode == "independent" else 1)
     value = total_steps / (ms * 1e-3)
     iter_ms = sum(a.elapsed_time(b) for a, b in it_ms) / len(it_ms)
     per_launch_ms = iter_ms / launches_per_iterate
@@ -283,15 +347,24 @@ def main():
     achieved_flops = map_steps_per_launch * FP64_FLOP_PER_STEP / (per_launch_ms * 1e-3)
     pipe_instr = map_steps_per_launch * FP64_INSTR_PER_STEP / (per_launch_ms * 1e-3)
     # The binding unit is the FP64 pipe: achieved = FP64 instructions per second
-    # of the dominant kernel (source count x map steps / CUDA-event launch time),
-    # peak = the live DFMA probe (one FP64 instruction per lane-slot).
+    # of the dominant kernel (source count x map steps / CUDA-event launch time);
+    # peak = the FP64 pipe's measured lane rate per SM per clock (the live DFMA
+    # probe, with the SM clock sampled while it ran) x SMs x the 2032 MHz maximum
+    # clock that the timed region ran at.  frac counts FP64 instructions (one
+    # pipe slot each, FMA or not); frac_flop counts FLOP (FMA = 2) against twice
+    # that rate.
     roofline = {"bound": "alu", "kernel": "k_iterate_fp64<7,true>",
-                "achieved": pipe_instr / 1e12, "peak": NOMINAL_FP64_INSTR_PER_S / 1e12, "unit": "T FP64-instr/s",
-                "frac": pipe_instr / NOMINAL_FP64_INSTR_PER_S, "traffic": traffic_for("k_iterate_fp64"),
-                "peak_source": "nominal: 1.25 TFLOP/s FP64 (148 SMs at 2032 MHz) / 2 FLOP per FMA",
-                "probe_peak": dfma / 1e12, "frac_of_probe": pipe_instr / dfma,
-                "probe_source": "measured live: DFMA probe (arnold_probe_peak), %.2f of the nominal"
-                                % (dfma / NOMINAL_FP64_INSTR_PER_S),
+                "achieved": pipe_instr / 1e12, "peak": dfma_peak / 1e12, "unit": "T FP64-instr/s",
+                "frac": pipe_instr / dfma_peak, "frac_flop": achieved_flops / (2.0 * dfma_peak),
+                "traffic": traffic_for("k_iterate_fp64"),
+                "peak_source": "measured: DFMA probe %.3f lanes/SM/clock at %s MHz x %d SMs x %d MHz"
+                               % (probes["dfma"]["ops_per_sm_per_clock"], probes["dfma"]["sm_mhz"], sms,
+                                  SM_MAX_MHZ),
+                "nominal_peak": NOMINAL_FP64_INSTR_PER_S / 1e12,
+                "frac_of_nominal": pipe_instr / NOMINAL_FP64_INSTR_PER_S,
+                "frac_flop_of_nominal": achieved_flops / (2.0 * NOMINAL_FP64_INSTR_PER_S),
+                "nominal_source": "1.25 TFLOP/s FP64 (the part's published figure) / 2 FLOP per FMA",
+                "probe": probes["dfma"],
                 "fp64_instr_per_map_step": FP64_INSTR_PER_STEP,
                 "fp64_tflops": achieved_flops / 1e12, "flop_per_map_step": FP64_FLOP_PER_STEP,
                 "issued_instr_per_map_step_ncu": FP64_ISSUED_PER_STEP_NCU,
@@ -305,7 +378,7 @@ def main():
     if rank == 0 or world > 1:
         raw = torch.empty((6, n), device="cuda", dtype=torch.float64)
         ens2 = ArnoldEnsemble(n, precision="fp64", device=local, stream=stream.cuda_stream)
-        ens2.init_grid(G, E, seed=rank, raw_out=raw)
+        ens2.init_grid(G, E, seed=seed, row0=row0, raw_out=raw)
         hx = raw[:3].cpu().pin_memory()
         hp = raw[3:].cpu().pin_memory()
         hchi = torch.empty(n, dtype=torch.float64).pin_memory()
@@ -323,7 +396,7 @@ def main():
             e2e_step()
         barrier()
         wt = time.perf_counter() - w0
-        e2e = {"value": n * args.chunk * k2 * world / wt, "unit": "map-steps/s",
+        e2e = {"value": n * args.chunk * k2 * world / wt, "unit": "map-steps/s",   # bands: n * world = G * G
                "h2d_bytes_per_step": int(hx.numel() * 8 + hp.numel() * 8), "d2h_bytes_per_step": int(hchi.numel() * 8),
                "steps": k2, "api": "ArnoldEnsemble.set_state/iterate/indicator (C ABI, host pinned buffers)"}
         ens2.close()
@@ -335,7 +408,7 @@ def main():
     fp32c = None
     df64 = None
     df64f = None
-    if not args.no_fp32c:
+    if extras and not args.no_fp32c:
         fp32c = precision_leg("fp32c", n, rank, local, stream, barrier, fp64_steps, chi64, cls64, value / world,
                               ffma, FP32C_INSTR_PER_STEP, FP32C_ISSUED_PER_STEP_NCU)
         df64 = precision_leg("df64", n, rank, local, stream, barrier, fp64_steps, chi64, cls64, value / world,
@@ -343,10 +416,10 @@ def main():
         df64f = precision_leg("df64f", n, rank, local, stream, barrier, fp64_steps, chi64, cls64, value / world,
                               ffma, None, None)
 
-    adjoint = None if args.no_extras else adjoint_leg(stream, local, barrier)
-    batch = None if args.no_extras else batch_leg(stream, local, barrier, args)
-    long_horizon = None if args.no_extras else long_horizon_leg(local, stream, barrier)
-    energies = None if args.no_extras else energies_leg(n, rank, local, stream, barrier, args.chunk)
+    adjoint = adjoint_leg(stream, local, barrier) if extras else None
+    batch = batch_leg(stream, local, barrier, args) if extras else None
+    long_horizon = long_horizon_leg(local, stream, barrier) if extras else None
+    energies = energies_leg(n, rank, local, stream, barrier, args.chunk) if extras else None
 
     if rank != 0:
         if dist:
@@ -354,11 +427,12 @@ def main():
         return
     cpu = cpu_oracle_rate(args.cpu_seconds) if world == 1 else None
     line = {"metric": METRIC, "value": value, "unit": "map-steps/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak" if mode == "independent" else "strong",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(args),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(gpu_launches),
             "clocks": clk.summary(), "fp32c": fp32c, "df64": df64, "df64f": df64f, "adjoint": adjoint, "batch": batch,
-            "energies": energies, "long_horizon": long_horizon, "probe": {"dfma_per_s": dfma, "ffma_per_s": ffma}}
+            "energies": energies, "long_horizon": long_horizon, "probe": probes}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -164,6 +164,33 @@ int arnold_init_grid(arnold_ctx* ctx, int64_t G, int64_t row0, double E, uint64_
 int arnold_set_state_shell(arnold_ctx* ctx, const double* x, const double* p, int mode, double E,
                            int ptr_kind);
 
+/* Initial conditions drawn on the device from SplitMix64(seed): candidate
+ * t = offset + k draws counters 5t .. 5t+4 (three angles uniform on the torus,
+ * then two uniforms u, w in [0, 1) for the momentum), the same stream as the
+ * host generator, so an ensemble can be built in pieces (offset) or sharded.
+ *
+ * arnold_init_sphere (Sec. IV, Figs. 2-3: ensembles uniform over the sphere S
+ * or a patch of it): trajectory k is candidate offset + k, with direction
+ * cos theta = cos_lo + (cos_hi - cos_lo) u, phi = phi_lo + (phi_hi - phi_lo) w
+ * and |P| = sqrt(2 (E - eps Hp(X))).  Resets the clock like arnold_set_state.
+ * Errors: EINVAL (offset < 0, E <= 2|eps|, a patch outside [-1, 1] or reversed),
+ * ECUDA. */
+int arnold_init_sphere(arnold_ctx* ctx, double E, uint64_t seed, int64_t offset, double cos_lo, double cos_hi,
+                       double phi_lo, double phi_hi);
+
+/* arnold_init_gaussian (Sec. IV, Fig. 4: the cloud injected at W): candidate t
+ * has (p_x, p_y) = (px0, py0) + sigma r (cos 2 pi w, sin 2 pi w) with
+ * r = sqrt(-2 ln(1 - u)) (Box-Muller) and p_z = +sqrt(2 (E - eps Hp) - p_x^2 -
+ * p_y^2); candidates whose radicand is negative have no real p_z and are
+ * skipped.  The n trajectories are the first n candidates from `offset` that
+ * have one, in candidate order; *n_drawn (if not NULL) receives the number of
+ * candidates examined up to the last one kept.  Synchronises the stream.
+ * Uses ~0.8 MB of library-owned device scratch (allocated on first use).
+ * Errors: EINVAL (offset < 0, sigma < 0, non-finite input), ERANGE (fewer than
+ * n real p_z among the first 64 n + 2^24 candidates), ENOMEM, ECUDA. */
+int arnold_init_gaussian(arnold_ctx* ctx, double E, double px0, double py0, double sigma, uint64_t seed,
+                         int64_t offset, int64_t* n_drawn);
+
 /* Area tracking (Sec. IV, Fig. 3 zooms: trajectories that leave the scanned
  * area are dropped): from now on, every renorm_every steps, a trajectory whose
  * momentum direction (cos theta = p_z/|P|, phi = atan2(p_y, p_x) in [0, 2pi))
@@ -374,8 +401,11 @@ const char* arnold_strerror(int status);
 int arnold_debug_sincos(arnold_ctx* ctx, int precision, int64_t n, const double* x, double* s,
                         double* c);
 
-/* Pipe-throughput probe on `device`: kind 0 = DFMA, 1 = FFMA, 2 = MUFU sin;
- * *ops_per_s receives lane-operations per second (best of 3).  Runs ~50 ms.
+/* Pipe-throughput probe on `device`: kind 0 = DFMA, 1 = FFMA, 2 = MUFU sin, at
+ * full occupancy with 8 independent chains per thread; *ops_per_s receives
+ * lane-operations per second (best of 6 launches of ~100 ms after ~300 ms of
+ * warm-up, so the clocks have risen; ~1 s in all).  Sample the SM clock while
+ * it runs to turn the rate into operations per SM per clock.
  * Errors: EINVAL, ECUDA, EUNSUPPORTED. */
 int arnold_probe_peak(int device, int kind, double* ops_per_s);
 

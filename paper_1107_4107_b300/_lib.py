@@ -65,6 +65,9 @@ SIGNATURES = {
     "arnold_iterate": (ctypes.c_int, [vp, i64]),
     "arnold_set_snapshots": (ctypes.c_int, [vp, vp, i64]),
     "arnold_set_state_shell": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_int]),
+    "arnold_init_sphere": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_uint64, i64] + [ctypes.c_double] * 4),
+    "arnold_init_gaussian": (ctypes.c_int, [vp] + [ctypes.c_double] * 4 + [ctypes.c_uint64, i64,
+                                                                          ctypes.POINTER(i64)]),
     "arnold_track_patch": (ctypes.c_int, [vp] + [ctypes.c_double] * 4),
     "arnold_velocity_histogram": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4 +
                                   [ctypes.c_int, vp, ctypes.c_int, ctypes.c_int]),

@@ -116,20 +116,23 @@ class ArnoldEnsemble:
             raise ValueError("X and P must both be host or both device")
         check(_lib.lib().arnold_set_state_shell(self._h, px, pp, int(mode), float(E), kx), "arnold_set_state_shell")
 
-    def init_sphere(self, E: float, seed: int = 0, cos_range=(-1.0, 1.0), phi_range=(0.0, 2 * math.pi)):
+    def init_sphere(self, E: float, seed: int = 0, cos_range=(-1.0, 1.0), phi_range=(0.0, 2 * math.pi),
+                    offset: int = 0):
         """Ensemble uniform over (a patch of) the momentum sphere S and over the
-        torus (Sec. IV, Figs. 2-3); directions drawn on the host (inputs module)."""
-        from .inputs import sphere_directions
-        X, nhat = sphere_directions(self.n, seed, cos_range, phi_range)
-        self.set_state_shell(X, nhat, _lib.SHELL_DIRECTION, E)
+        torus (Sec. IV, Figs. 2-3), drawn on the device (arnold_init_sphere)."""
+        check(_lib.lib().arnold_init_sphere(self._h, float(E), int(seed), int(offset), float(cos_range[0]),
+                                            float(cos_range[1]), float(phi_range[0]), float(phi_range[1])),
+              "arnold_init_sphere")
 
-    def init_gaussian(self, E: float, center, sigma: float = 0.01, seed: int = 0):
-        """Gaussian cloud in (p_x, p_y) about `center`, p_z from the energy (Fig. 4)."""
-        from .inputs import gaussian_velocities
-        X, Pxy = gaussian_velocities(self.n, center, sigma, seed)
-        P = np.zeros((3, self.n))
-        P[:2] = Pxy
-        self.set_state_shell(X, P, _lib.SHELL_PZ, E)
+    def init_gaussian(self, E: float, center, sigma: float = 0.01, seed: int = 0, offset: int = 0) -> int:
+        """Gaussian cloud in (p_x, p_y) about `center`, p_z from the energy (Fig. 4),
+        drawn on the device; draws without a real p_z are skipped, so the ensemble
+        holds the first n draws that have one.  Returns the number of draws
+        examined."""
+        drawn = _lib.i64()
+        check(_lib.lib().arnold_init_gaussian(self._h, float(E), float(center[0]), float(center[1]), float(sigma),
+                                              int(seed), int(offset), ctypes.byref(drawn)), "arnold_init_gaussian")
+        return drawn.value
 
     def track_patch(self, cos_lo: float, cos_hi: float, phi_lo: float, phi_hi: float):
         check(_lib.lib().arnold_track_patch(self._h, cos_lo, cos_hi, phi_lo, phi_hi), "arnold_track_patch")

@@ -103,6 +103,7 @@ struct arnold_ctx {
   long long adj_N = 0, adj_C = 0, adj_K = 0;
   unsigned long long* vhist = nullptr;   // device counts for host-side histograms
   size_t vhist_cells = 0;
+  void* draw = nullptr;                  // Gaussian redraw scratch: block counts, offsets, kept, drawn (lazy)
 };
 
 namespace {
@@ -253,7 +254,7 @@ void free_all(arnold_ctx* c) {
   void* ptrs[] = {c->s.st, c->s.tg, c->s.lap, c->s.lapref, c->s.ref, c->s.logsum, c->s.demax, c->s.e0, c->s.V,
                   c->f.hi, c->f.lo, c->f.tg, c->sc, c->th, c->scf, c->scd, c->flags, c->partials, c->stats_out,
                   c->scratch, c->scratch2, c->ck, c->seg, c->lam, c->lamf, c->gh, c->ge, c->sum_part, c->s.left,
-                  c->vhist, c->s.megno, c->f.tg_lo};
+                  c->vhist, c->s.megno, c->f.tg_lo, c->draw};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -561,6 +562,70 @@ int arnold_init_grid(arnold_ctx* c, int64_t G, int64_t row0, double E, uint64_t 
   c->adj_valid = 0;
   ACHECK(launch_init_grid(a, grid_for(c, 256), 256, c->stream));
   c->launches++;
+  c->steps = 0;
+  return ARNOLD_OK;
+}
+
+int arnold_init_sphere(arnold_ctx* c, double E, uint64_t seed, int64_t offset, double cos_lo, double cos_hi,
+                       double phi_lo, double phi_hi) {
+  if (!c || offset < 0 || !isfinite(E) || !(E > 2.0 * fabs(c->prm.eps))) return ARNOLD_EINVAL;
+  if (!(cos_lo >= -1.0 && cos_lo <= cos_hi && cos_hi <= 1.0) || !(phi_lo <= phi_hi) || !isfinite(phi_lo + phi_hi))
+    return ARNOLD_EINVAL;
+  ACHECK(cudaSetDevice(c->device));
+  InitArgs a = init_args(c);
+  a.E = E;
+  a.seed = seed;
+  a.shell_mode = 1;
+  ACHECK(cudaMemsetAsync(c->flags, 0, sizeof(int), c->stream));
+  c->adj_valid = 0;
+  const double p4[4] = {cos_lo, cos_hi, phi_lo, phi_hi};
+  ACHECK(launch_init_sphere(a, (unsigned long long)offset, p4, grid_for(c, 256), c->stream));
+  c->launches++;
+  c->steps = 0;
+  return ARNOLD_OK;
+}
+
+int arnold_init_gaussian(arnold_ctx* c, double E, double px0, double py0, double sigma, uint64_t seed,
+                         int64_t offset, int64_t* n_drawn) {
+  if (!c || offset < 0 || !isfinite(E) || !isfinite(px0) || !isfinite(py0) || !(sigma >= 0.0) || !isfinite(sigma))
+    return ARNOLD_EINVAL;
+  ACHECK(cudaSetDevice(c->device));
+  const int kMaxBlocks = 65536;   // candidates per chunk: 256 per block
+  const size_t bytes = (size_t)kMaxBlocks * (sizeof(int) + sizeof(long long)) + 2 * sizeof(long long);
+  if (!c->draw) ACHECK(cudaMalloc(&c->draw, bytes));
+  int* counts = (int*)c->draw;
+  long long* offs = (long long*)(counts + kMaxBlocks);
+  long long* have_d = offs + kMaxBlocks;
+  unsigned long long* drawn_d = (unsigned long long*)(have_d + 1);
+  ACHECK(cudaMemsetAsync(have_d, 0, 2 * sizeof(long long), c->stream));
+  ACHECK(cudaMemsetAsync(c->flags, 0, sizeof(int), c->stream));
+  c->adj_valid = 0;
+  InitArgs a = init_args(c);
+  a.E = E;
+  a.seed = seed;
+  a.shell_mode = 2;
+  unsigned long long t0 = (unsigned long long)offset;
+  long long kept = 0;
+  // give up when almost no draw has a real p_z (the cloud lies outside the shell)
+  const unsigned long long limit = 64ULL * (unsigned long long)c->n + (1ULL << 24);
+  long long nb = 0;
+  while (kept < c->n) {
+    if (t0 - (unsigned long long)offset > limit) return ARNOLD_ERANGE;
+    // twice the candidates still needed, and at least twice the last chunk (few
+    // real p_z: the chunks grow geometrically to the 2^24-candidate cap)
+    const long long need = (2 * (c->n - kept) + 255) / 256;
+    nb = need > 2 * nb ? need : 2 * nb;
+    nb = nb < 4 ? 4 : (nb > kMaxBlocks ? kMaxBlocks : nb);
+    ACHECK(launch_gauss_chunk(a, t0, (int)nb, px0, py0, sigma, counts, offs, have_d, drawn_d, c->stream));
+    c->launches += 3;
+    ACHECK(cudaMemcpyAsync(&kept, have_d, sizeof kept, cudaMemcpyDeviceToHost, c->stream));
+    ACHECK(cudaStreamSynchronize(c->stream));
+    t0 += (unsigned long long)nb * 256ULL;
+  }
+  unsigned long long drawn = 0;
+  ACHECK(cudaMemcpyAsync(&drawn, drawn_d, sizeof drawn, cudaMemcpyDeviceToHost, c->stream));
+  ACHECK(cudaStreamSynchronize(c->stream));
+  if (n_drawn) *n_drawn = (int64_t)(drawn - (unsigned long long)offset);
   c->steps = 0;
   return ARNOLD_OK;
 }
@@ -984,23 +1049,33 @@ int arnold_probe_peak(int device, int kind, double* ops) {
   ACHECK(cudaSetDevice(device));
   int sms = 0;
   ACHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  // full occupancy (8 x 256 threads per SM), 8 independent chains per thread
   const int block = 256, grid = sms * 8;
-  const int iters = kind == 0 ? 2048 : (kind == 1 ? 65536 : 16384);
   double* sink = nullptr;
   ACHECK(cudaMalloc(&sink, sizeof(double) * (size_t)grid * block));
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  float best = 1e30f;
-  cudaError_t err = launch_probe(kind, grid, block, 16, sink, 0);
-  for (int r = 0; r < 4 && err == cudaSuccess; ++r) {
-    cudaEventRecord(e0, 0);
-    err = launch_probe(kind, grid, block, iters, sink, 0);
-    cudaEventRecord(e1, 0);
+  // size one launch to ~100 ms from a short one, run ~300 ms to bring the clocks
+  // up, then keep the best of 6 timed launches (~0.6 s)
+  int iters = kind == 0 ? 256 : (kind == 1 ? 8192 : 2048);
+  float ms = 0.f, best = 1e30f;
+  cudaError_t err = cudaEventRecord(e0, 0);
+  if (err == cudaSuccess) err = launch_probe(kind, grid, block, iters, sink, 0);
+  if (err == cudaSuccess) err = cudaEventRecord(e1, 0);
+  if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+  if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+  if (err == cudaSuccess && ms > 0.f) {
+    const double scale = 100.0 / ms;
+    iters = (int)fmin(fmax(iters * scale, 16.0), 1.0e8);
+  }
+  for (int r = 0; r < 9 && err == cudaSuccess; ++r) {
+    err = cudaEventRecord(e0, 0);
+    if (err == cudaSuccess) err = launch_probe(kind, grid, block, iters, sink, 0);
+    if (err == cudaSuccess) err = cudaEventRecord(e1, 0);
     if (err == cudaSuccess) err = cudaEventSynchronize(e1);
-    float ms = 0.f;
-    if (err == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
-    if (r > 0 && ms > 0.f && ms < best) best = ms;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    if (err == cudaSuccess && r >= 3 && ms > 0.f && ms < best) best = ms;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

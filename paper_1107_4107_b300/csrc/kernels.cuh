@@ -83,6 +83,12 @@ cudaError_t launch_set_state(const InitArgs& a, int grid, int block, cudaStream_
 cudaError_t launch_vhist(long long n, const double* V, const unsigned char* left, int filtered, const double* patch4,
                          int n_cos, int n_phi, unsigned long long* counts, int grid, cudaStream_t st);
 cudaError_t launch_init_grid(const InitArgs& a, int grid, int block, cudaStream_t st);
+cudaError_t launch_init_sphere(const InitArgs& a, unsigned long long offset, const double* patch4, int grid,
+                               cudaStream_t st);
+// One chunk of 256 * nb Gaussian candidates from t0: count, prefix, place.
+cudaError_t launch_gauss_chunk(const InitArgs& a, unsigned long long t0, int nb, double cx, double cy, double sigma,
+                               int* counts, long long* offs, long long* have, unsigned long long* drawn,
+                               cudaStream_t st);
 cudaError_t launch_indicator(const ReadArgs& a, int grid, int block, cudaStream_t st);
 cudaError_t launch_debug_sincos64(const double* x, double* s, double* c, long long n, const double2* sc,
                                   const double* th, cudaStream_t st);

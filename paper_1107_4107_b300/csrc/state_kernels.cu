@@ -92,37 +92,173 @@ __device__ __forceinline__ void init_common(const InitArgs& a, long long i, doub
   }
 }
 
+// One trajectory from the paper's (X, P): angles reduced, rotated coordinates,
+// and for shell modes the fixed-energy momentum (Sec. IV): mode 1 scales the
+// unit direction (px, py, pz) to |P| = sqrt(2 (E - eps Hp)), mode 2 sets
+// p_z = +sqrt(2 (E - eps Hp) - p_x^2 - p_y^2).
+__device__ __forceinline__ void set_one(const InitArgs& a, long long i, double x, double y, double z, double px,
+                                        double py, double pz, int mode) {
+  reduce_any(x);
+  reduce_any(y);
+  const int lz = reduce_any(z);
+  double u, v;
+  int lu, lv;
+  to_uv(x, y, u, v, lu, lv);
+  if (mode) {   // fixed-energy initial momenta (Sec. IV)
+    double su, cu, sv, cv, sz, cz;
+    sincos_tab64(u, a.sc, a.th, su, cu);
+    sincos_tab64(v, a.sc, a.th, sv, cv);
+    sincos_tab64(z, a.sc, a.th, sz, cz);
+    const double hp = (cu + cv) * (cz * cz);
+    if (mode == 1) {          // P = sqrt(2 (E - eps Hp)) * unit direction
+      const double r = 2.0 * (a.E - a.eps * hp);
+      const double m = sqrt(r);
+      if (!(r >= 0.0)) atomicOr(a.flags, kFlagNonFinite);
+      px *= m; py *= m; pz *= m;
+    } else {                  // p_z = +sqrt(2 (E - eps Hp) - p_x^2 - p_y^2)
+      const double r = 2.0 * (a.E - a.eps * hp) - px * px - py * py;
+      pz = sqrt(r);
+      if (!(r >= 0.0)) atomicOr(a.flags, kFlagNonFinite);
+    }
+  }
+  // the parity of lu + lv carries the pi offset of x and y; displacements
+  // are measured from here, so earlier laps of x and y are not kept
+  init_common(a, i, u, v, z, px + py, px - py, pz, lu, lv, lz);
+}
+
 __global__ void k_set_state(InitArgs a) {
   const long long n = a.n;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    set_one(a, i, a.x_in[i], a.x_in[n + i], a.x_in[2 * n + i], a.p_in[i], a.p_in[n + i], a.p_in[2 * n + i],
+            a.shell_mode);
+}
+
+// ---- initial conditions drawn on the device (Sec. IV, Figs. 2-4) ----------
+// Candidate t draws SplitMix64(seed) counters 5t .. 5t+4, as the host generator
+// does: three angles uniform on the torus, then two uniforms for the momentum.
+
+__device__ __forceinline__ double uniform01_dev(unsigned long long r) {
+  return __dmul_rn((double)(r >> 11), 1.1102230246251565404236316680908203125e-16);
+}
+
+// Sphere ensemble (Figs. 2-3): direction with cos theta uniform in
+// [cos_lo, cos_hi] and phi uniform in [phi_lo, phi_hi]; |P| from the energy.
+__global__ void k_init_sphere(InitArgs a, unsigned long long offset, double cos_lo, double cos_hi, double phi_lo,
+                              double phi_hi) {
+  const long long n = a.n;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    double x = a.x_in[i], y = a.x_in[n + i], z = a.x_in[2 * n + i];
-    reduce_any(x);
-    reduce_any(y);
-    const int lz = reduce_any(z);
-    double u, v;
-    int lu, lv;
-    to_uv(x, y, u, v, lu, lv);
-    double px = a.p_in[i], py = a.p_in[n + i], pz = a.p_in[2 * n + i];
-    if (a.shell_mode) {   // fixed-energy initial momenta (Sec. IV)
-      double su, cu, sv, cv, sz, cz;
-      sincos_tab64(u, a.sc, a.th, su, cu);
-      sincos_tab64(v, a.sc, a.th, sv, cv);
-      sincos_tab64(z, a.sc, a.th, sz, cz);
-      const double hp = (cu + cv) * (cz * cz);
-      if (a.shell_mode == 1) {          // P = sqrt(2 (E - eps Hp)) * unit direction
-        const double r = 2.0 * (a.E - a.eps * hp);
-        const double m = sqrt(r);
-        if (!(r >= 0.0)) atomicOr(a.flags, kFlagNonFinite);
-        px *= m; py *= m; pz *= m;
-      } else {                          // p_z = +sqrt(2 (E - eps Hp) - p_x^2 - p_y^2)
-        const double r = 2.0 * (a.E - a.eps * hp) - px * px - py * py;
-        pz = sqrt(r);
-        if (!(r >= 0.0)) atomicOr(a.flags, kFlagNonFinite);
-      }
+    const unsigned long long c = 5ULL * (offset + (unsigned long long)i);
+    const double x = uniform_angle(splitmix64(a.seed, c));
+    const double y = uniform_angle(splitmix64(a.seed, c + 1));
+    const double z = uniform_angle(splitmix64(a.seed, c + 2));
+    const double u = uniform01_dev(splitmix64(a.seed, c + 3));
+    const double w = uniform01_dev(splitmix64(a.seed, c + 4));
+    const double ct = cos_lo + (cos_hi - cos_lo) * u;
+    const double ph = phi_lo + (phi_hi - phi_lo) * w;
+    const double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+    double sp, cp;
+    sincos(ph, &sp, &cp);
+    set_one(a, i, x, y, z, st * cp, st * sp, ct, 1);
+  }
+}
+
+// Gaussian cloud of Fig. 4: (p_x, p_y) = centre + sigma r (cos 2 pi u2, sin 2 pi u2),
+// r = sqrt(-2 ln u1), u1 in (0, 1] (Box-Muller); p_z from the energy.  Returns
+// whether the energy condition has a real p_z, and the candidate's values.
+struct Cand { double x, y, z, px, py; };
+
+__device__ __forceinline__ bool gauss_candidate(const InitArgs& a, unsigned long long t, double cx, double cy,
+                                                double sigma, Cand& k) {
+  const unsigned long long c = 5ULL * t;
+  k.x = uniform_angle(splitmix64(a.seed, c));
+  k.y = uniform_angle(splitmix64(a.seed, c + 1));
+  k.z = uniform_angle(splitmix64(a.seed, c + 2));
+  const double u1 = 1.0 - uniform01_dev(splitmix64(a.seed, c + 3));
+  const double u2 = uniform01_dev(splitmix64(a.seed, c + 4));
+  const double r = sqrt(-2.0 * log(u1));
+  double s2, c2;
+  sincos(kTwoPi * u2, &s2, &c2);
+  k.px = cx + sigma * r * c2;
+  k.py = cy + sigma * r * s2;
+  // the energy condition as set_one evaluates it (the same angles, the same
+  // rotated-coordinate sincos), so "valid" here means a real p_z there
+  double x = k.x, y = k.y, u, v;
+  int lu, lv;
+  to_uv(x, y, u, v, lu, lv);
+  double su, cu, sv, cv, sz, cz;
+  sincos_tab64(u, a.sc, a.th, su, cu);
+  sincos_tab64(v, a.sc, a.th, sv, cv);
+  sincos_tab64(k.z, a.sc, a.th, sz, cz);
+  const double hp = (cu + cv) * (cz * cz);
+  return 2.0 * (a.E - a.eps * hp) - k.px * k.px - k.py * k.py >= 0.0;
+}
+
+constexpr int kDrawBlock = 256;
+
+// Pass 1: valid candidates among t0 + [b * 256, (b + 1) * 256), per block.
+__global__ void __launch_bounds__(kDrawBlock) k_gauss_count(InitArgs a, unsigned long long t0, double cx, double cy,
+                                                            double sigma, int* counts) {
+  __shared__ int s_warp[kDrawBlock / 32];
+  Cand k;
+  const bool ok = gauss_candidate(a, t0 + (unsigned long long)blockIdx.x * kDrawBlock + threadIdx.x, cx, cy, sigma, k);
+  const unsigned int m = __ballot_sync(0xFFFFFFFFu, ok);
+  if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = __popc(m);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int w = 0; w < kDrawBlock / 32; ++w) s += s_warp[w];
+    counts[blockIdx.x] = s;
+  }
+}
+
+// Pass 2 (one block): exclusive prefix of the block counts, starting at the
+// number already kept (*have), in block order; *have becomes the new total.
+__global__ void __launch_bounds__(1024) k_gauss_scan(const int* counts, int nb, long long* offs, long long* have) {
+  __shared__ long long s_part[1024];
+  const int per = (nb + 1023) / 1024;
+  const int lo = threadIdx.x * per, hi = min(nb, lo + per);
+  long long s = 0;
+  for (int b = lo; b < hi; ++b) s += counts[b];
+  s_part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {   // 1024 partial sums: a plain sequential prefix, once
+    long long acc = *have;
+    for (int k = 0; k < 1024; ++k) {
+      const long long v = s_part[k];
+      s_part[k] = acc;
+      acc += v;
     }
-    // the parity of lu + lv carries the pi offset of x and y; displacements
-    // are measured from here, so earlier laps of x and y are not kept
-    init_common(a, i, u, v, z, px + py, px - py, pz, lu, lv, lz);
+    *have = acc;
+  }
+  __syncthreads();
+  long long acc = s_part[threadIdx.x];
+  for (int b = lo; b < hi; ++b) {
+    offs[b] = acc;
+    acc += counts[b];
+  }
+}
+
+// Pass 3: each valid candidate goes to slot offs[block] + its rank within the
+// block (candidate order), while slots remain; the candidate that fills the
+// last slot records its index + 1 in *drawn.
+__global__ void __launch_bounds__(kDrawBlock) k_gauss_place(InitArgs a, unsigned long long t0, double cx, double cy,
+                                                            double sigma, const long long* offs,
+                                                            unsigned long long* drawn) {
+  __shared__ int s_warp[kDrawBlock / 32];
+  const unsigned long long t = t0 + (unsigned long long)blockIdx.x * kDrawBlock + threadIdx.x;
+  Cand k;
+  const bool ok = gauss_candidate(a, t, cx, cy, sigma, k);
+  const unsigned int m = __ballot_sync(0xFFFFFFFFu, ok);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) s_warp[warp] = __popc(m);
+  __syncthreads();
+  int before = 0;
+  for (int w = 0; w < warp; ++w) before += s_warp[w];
+  before += __popc(m & ((1u << lane) - 1u));
+  const long long slot = offs[blockIdx.x] + before;
+  if (ok && slot < a.n) {
+    set_one(a, slot, k.x, k.y, k.z, k.px, k.py, 0.0, 2);
+    if (slot == a.n - 1) *drawn = t + 1;
   }
 }
 
@@ -370,6 +506,25 @@ cudaError_t launch_vhist(long long n, const double* V, const unsigned char* left
 
 cudaError_t launch_set_state(const InitArgs& a, int grid, int block, cudaStream_t st) {
   k_set_state<<<grid, block, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_sphere(const InitArgs& a, unsigned long long offset, const double* patch4, int grid,
+                               cudaStream_t st) {
+  k_init_sphere<<<grid, 256, 0, st>>>(a, offset, patch4[0], patch4[1], patch4[2], patch4[3]);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gauss_chunk(const InitArgs& a, unsigned long long t0, int nb, double cx, double cy, double sigma,
+                               int* counts, long long* offs, long long* have, unsigned long long* drawn,
+                               cudaStream_t st) {
+  k_gauss_count<<<nb, kDrawBlock, 0, st>>>(a, t0, cx, cy, sigma, counts);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_gauss_scan<<<1, 1024, 0, st>>>(counts, nb, offs, have);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_gauss_place<<<nb, kDrawBlock, 0, st>>>(a, t0, cx, cy, sigma, offs, drawn);
   return cudaGetLastError();
 }
 

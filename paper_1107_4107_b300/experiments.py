@@ -17,7 +17,6 @@ import os
 
 import numpy as np
 
-from . import _lib
 from .api import ArnoldEnsemble
 from .params import paper_h
 
@@ -140,34 +139,11 @@ def _load_fig4_ckpt(path: str, e: ArnoldEnsemble, bounds, shape):
 
 
 def init_gaussian_valid(n: int, E: float, center, sigma: float, seed: int, **kw) -> ArnoldEnsemble:
-    """Gaussian cloud with p_z from the energy, redrawing the draws whose energy
-    condition has no real solution: candidates are placed on the device, those
-    with finite p_z kept in order until n are found."""
-    from .inputs import gaussian_velocities
-    Xs, Ps = [], []
-    have, offset, batch = 0, 0, max(2 * n, 1024)
-    probe = ArnoldEnsemble(batch, tangent=False, device=kw.get("device", 0))
-    while have < n:
-        X, Pxy = gaussian_velocities(batch, center, sigma, seed, offset=offset)
-        P = np.zeros((3, batch))
-        P[:2] = Pxy
-        probe.set_state_shell(X, P, _lib.SHELL_PZ, E)
-        # read through a device buffer: the host read would report the
-        # (expected) non-finite candidates as an error
-        import torch
-        Pd = torch.empty((3, batch), device=f"cuda:{kw.get('device', 0)}", dtype=torch.float64)
-        probe.indicator("P", out=Pd)
-        Pfull = Pd.cpu().numpy()
-        ok = np.isfinite(Pfull[2])
-        Xs.append(X[:, ok])
-        Ps.append(Pfull[:, ok])
-        have += int(ok.sum())
-        offset += batch
-    probe.close()
-    X = np.ascontiguousarray(np.concatenate(Xs, axis=1)[:, :n])
-    P = np.ascontiguousarray(np.concatenate(Ps, axis=1)[:, :n])
+    """Gaussian cloud with p_z from the energy (Fig. 4), drawn on the device:
+    draws whose energy condition has no real solution are skipped, the first n
+    that have one are kept in draw order (arnold_init_gaussian)."""
     e = ArnoldEnsemble(n, tangent=False, **kw)
-    e.set_state(X, P)
+    e.init_gaussian(E, center, sigma, seed)
     return e
 
 

@@ -1,7 +1,7 @@
 """A small, fixed case of the hot path for profilers (ncu) and quick timing.
 
     python -m paper_1107_4107_b300.profile_case --precision fp64 --n 1048576 --steps 20 --launches 3
-    python -m paper_1107_4107_b300.profile_case --batch 0.01 --launches 2
+    python -m paper_1107_4107_b300.profile_case --batch 0.01 --launches 2 [--batch-precision df64f]
 
 Grid-slice ICs at E = 400 (the scan's initial conditions on a sqrt(n)-wide
 band of the 2048-wide grid), then `launches` calls of iterate(steps), each one
@@ -24,8 +24,9 @@ def main():
                     help="instead: the FP64/FP32C adjoint of the variance loss over --steps steps of --n box "
                          "trajectories with checkpoints every C steps (one k_adjoint launch per segment)")
     ap.add_argument("--batch", type=float, default=0.0, metavar="SCALE",
-                    help="instead: the 64-set batch (FP32C) with steps scaled by SCALE and a fixed tuning "
+                    help="instead: the 64-set batch with steps scaled by SCALE and a fixed tuning "
                          "(block 128, 1 trajectory per thread, R 200, 200 ms epochs): --launches graph runs")
+    ap.add_argument("--batch-precision", default="fp32c", choices=["fp32c", "df64f", "df64"])
     a = ap.parse_args()
     import torch
     from .api import ArnoldEnsemble
@@ -34,7 +35,7 @@ def main():
         from .api import ArnoldBatch
         b = ArnoldBatch(params.batch_sets(step_scale=a.batch),
                         tuning={"block_size": 128, "traj_per_thread": 1, "renorm_every": 200, "epoch_ms": 200},
-                        stream=torch.cuda.current_stream().cuda_stream)
+                        stream=torch.cuda.current_stream().cuda_stream, precision=a.batch_precision)
         times = []
         for _ in range(a.launches):
             b.init()
@@ -46,7 +47,7 @@ def main():
             times.append(e0.elapsed_time(e1))
         b.sync()
         info = b.info()
-        print(json.dumps({"batch": a.batch, "ms": times, "epochs": info["epochs"], "items": info["items"],
+        print(json.dumps({"batch": a.batch, "precision": a.batch_precision, "ms": times, "epochs": info["epochs"], "items": info["items"],
                           "map_steps_per_s": info["map_steps_per_run"] / (min(times) * 1e-3)}))
         return
     if a.adjoint:

@@ -77,3 +77,24 @@ def growth_scaled(got, ref, growth, bound, power=1):
         err = np.max(err, axis=0)
     bar = bound * np.asarray(growth, dtype=np.float64) ** power
     return bool(np.all(err <= bar)), float(np.max(err / bar))
+
+
+def advance_with_growth_history(st, n_steps, threads=1):
+    """Advance the oracle state n_steps (a multiple of its renormalisation
+    interval R) and return each cell's largest tangent growth over any
+    sub-interval between renormalisations, max_k exp(L_k - min_{j<=k} L_j)
+    (L_k the log sum after k renormalisations, L_0 = 0).  ln|w| is not monotone:
+    after a chaotic transient the tangent can shrink again, so the final
+    exp(chi t) can understate how much an error made along the way was
+    stretched; this maximum does not."""
+    R = st.params.renorm_every
+    if n_steps % R:
+        raise ValueError("n_steps must be a multiple of the renormalisation interval")
+    L0 = st.logsum.copy()
+    low = L0.copy()
+    best = np.zeros(st.n)
+    for _ in range(n_steps // R):
+        st.advance(R, threads=threads)
+        low = np.minimum(low, st.logsum)
+        best = np.maximum(best, st.logsum - low)
+    return np.exp(np.minimum(best, 700.0))

@@ -282,23 +282,32 @@ def test_oracle_scale_scan_128x128_1e4_steps(torch_cuda, E):
     """The whole oracle-scale scan (128 x 128 grid, 16,384 trajectories, 1e4 steps with
     tangent) against the oracle run of the same configuration.  Past the Lyapunov time
     chaotic trajectories decorrelate, so the bar is the scan-level one: class agreement
-    >= 99.5 %, chi-histogram L1 <= 1e-2; every cell also agrees on the log sum of the
-    tangent to 1e-10 times its own tangent growth exp(chi t) (the first-order
-    propagation bound, with the 1e4-step sum of roundings)."""
+    >= 99.5 %, chi-histogram L1 <= 1e-2.  Every cell also agrees on the log sum of
+    the tangent to 1e-11 A^2, A the largest growth its tangent went through over
+    any stretch of the run (from the oracle's log sums at the renormalisations;
+    after a chaotic transient the tangent can shrink again, so the final
+    exp(chi t) understates it).  The log sum is a tangent quantity: a state
+    error reaches it through the Hessian along the path, hence the square, as
+    for the tangent components' 1e-12 G^2 over 1000 steps, here over ten times
+    the steps."""
     import os
     G = 128
     ens = _ens(G * G)
     ens.init_grid(G, E)
     ens.iterate(10000)
-    st = oracle_grid_state(G, E, oracle_params()).advance(10000, threads=max(1, os.cpu_count() or 1))
+    from parity import advance_with_growth_history
+    st = oracle_grid_state(G, E, oracle_params())
+    amp = advance_with_growth_history(st, 10000, threads=max(1, os.cpu_count() or 1))
     cls, chi = ens.indicator("class"), ens.indicator("chi")
     agree = float(np.mean(cls == st.classify()))
     l1 = _hist_l1(chi, st.chi())
-    from parity import cell_growth
-    g = cell_growth(st)
-    ratio = float(np.max(np.abs(chi - st.chi()) * st.time() / (1e-10 * g)))
+    dlog = np.abs(chi - st.chi()) * st.time()
+    bar = 1e-11 * amp ** 2
+    ratio = float(np.max(dlog / bar))
+    k = int(np.argmax(dlog / bar))
     print(f"E={E}: agreement {agree:.5f}, L1 {l1:.2e}, chaotic {cls.mean():.4f}, "
-          f"max |d log sum| / (1e-10 exp(chi t)) = {ratio:.2e}")
+          f"max |d log sum| / (1e-11 A^2) = {ratio:.2e} (cell {k}: d {dlog[k]:.2e}, "
+          f"A {amp[k]:.3g}, exp(chi t) {math.exp(min(700.0, st.chi()[k] * st.time())):.3g})")
     assert agree >= 0.995
     assert l1 <= 1e-2
     assert ratio <= 1.0

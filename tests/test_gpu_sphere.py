@@ -122,3 +122,50 @@ def test_tracked_run_resumes_bitwise_from_checkpoint(precision):
         with pytest.raises(ArnoldError) as ex:
             c.restore(blob)
         assert ex.value.status == EINVAL
+
+
+@pytest.mark.parametrize("precision", ["fp64", "df64f"])
+def test_device_sphere_draws_match_the_generator(precision):
+    """arnold_init_sphere draws the host generator's counters on the device: angles
+    equal, momenta on the energy shell along the generator's directions (CUDA sin/cos
+    of phi against libm: ~1e-16), for a patch and an offset into the stream."""
+    from parity import angle_dist
+    n, E, off = 5000, 400.0, 123457
+    patch = (-0.3, 0.8, 0.5, 4.0)
+    X, nh = inputs.sphere_directions(n, seed=21, cos_range=patch[:2], phi_range=patch[2:], offset=off)
+    e = _ens(n, precision=precision)
+    e.init_sphere(E, seed=21, cos_range=patch[:2], phi_range=patch[2:], offset=off)
+    tol = 1e-14 if precision == "fp64" else 1e-13
+    assert np.max(angle_dist(e.indicator("X"), X)) < tol
+    assert rel_err(e.indicator("P"), oracle.momenta_on_shell(E, 1.0, X, nh)) < tol
+    assert np.max(e.indicator("dE")) < 1e-12 * E
+    e.sync()
+
+
+def test_device_gaussian_keeps_exactly_the_draws_with_a_real_pz():
+    """arnold_init_gaussian at W = (sqrt E, sqrt E, 0), E = 15 (Fig. 4), where the
+    energy condition rejects many draws: the ensemble holds the first n draws that
+    the oracle's own energy condition accepts, in order, and reports how many draws
+    it examined; an offset continues the stream; a cloud off the shell is ERANGE."""
+    from paper_1107_4107_b300._lib import ArnoldError, ERANGE
+    from parity import angle_dist
+    n, E, sigma = 3000, 15.0, 0.01
+    W = math.sqrt(E)
+    for off in (0, 77777):
+        cand = 4 * n
+        X, Pxy = inputs.gaussian_velocities(cand, (W, W), sigma, seed=5, offset=off)
+        P = np.zeros((3, cand))
+        P[:2] = Pxy
+        Po = oracle.pz_from_energy(E, 1.0, X, P)
+        ok = np.isfinite(Po[2])
+        assert 0.05 < ok.mean() < 0.95 and ok.sum() >= n
+        e = _ens(n, tangent=False)
+        drawn = e.init_gaussian(E, (W, W), sigma, seed=5, offset=off)
+        assert drawn == int(np.nonzero(ok)[0][n - 1]) + 1
+        assert np.max(angle_dist(e.indicator("X"), X[:, ok][:, :n])) < 1e-14
+        assert rel_err(e.indicator("P"), Po[:, ok][:, :n]) < 1e-13
+        e.sync()
+    e = _ens(64, tangent=False)
+    with pytest.raises(ArnoldError) as ex:
+        e.init_gaussian(E, (10.0, 10.0), sigma, seed=5)
+    assert ex.value.status == ERANGE

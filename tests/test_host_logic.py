@@ -193,3 +193,74 @@ def test_arnold_map_is_one_autograd_function():
     assert api.ArnoldMap is F
     with pytest.raises(AttributeError):
         api.NoSuchName  # noqa: B018
+
+
+class _OracleBand:
+    """Stand-in for ArnoldEnsemble on the CPU (the oracle), holding one band of
+    rows of a grid scan, with the calls bench.bench_step makes."""
+
+    def __init__(self, G, E, row0, rows, seed):
+        X, Pxy = inputs.grid_slice(G, E, 1.0, seed=seed, rows=(row0, row0 + rows))
+        P = np.zeros((3, X.shape[1]))
+        P[:2] = Pxy
+        self.st = oracle.State(X, oracle.pz_from_energy(E, 1.0, X, P), oracle.Params())
+
+    def iterate(self, k):
+        self.st.advance(k)
+
+    def indicator(self, kind, out):
+        val = {"chi": self.st.chi, "class": self.st.classify, "V": self.st.velocity,
+               "dE_max": lambda: self.st.dE_max}[kind]()
+        out[...] = val
+
+    def stats(self):
+        s = oracle.stats(self.st.chi(), self.st.dE_max, self.st.P, self.st.time())
+        s["n"] = self.st.n
+        return s
+
+
+def _bench_band_rank(rank, world, port, out_path, G, E, chunk):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    row0, rows, seed = bench.rank_workload(world, rank, "band", grid=G)
+    ens = _OracleBand(G, E, row0, rows, seed)
+    n = rows * G
+    outs = {"chi": np.empty(n), "class": np.empty(n, dtype=np.uint8), "V": np.empty((3, n)), "dE_max": np.empty(n)}
+    bench.bench_step(ens, chunk, outs, gather=None)          # a first chunk without exchange
+    merged = bench.bench_step(ens, chunk, outs, gather=shard.gather_stats)
+    if rank == 0:
+        np.save(out_path, np.concatenate([merged["hist"], [merged["under"], merged["over"], merged["chaotic"],
+                                                            merged["n"], merged["dE_max"]],
+                                          merged["p_mean"], merged["p_var"]]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_bench_banded_scan_on_two_gloo_ranks(tmp_path):
+    """The bench's N > 1 path (rank_workload's row bands, bench_step's statistics
+    merge over the process group) on two CPU ranks with the oracle in place of the
+    GPU ensemble: the merged statistics of the banded scan equal those of the
+    whole scan run in one piece."""
+    import socket
+
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    G, E, chunk = 15, 40.0, 60
+    out = str(tmp_path / "band.npy")
+    mp.start_processes(_bench_band_rank, args=(2, port, out, G, E, chunk), nprocs=2, join=True,
+                       start_method="spawn")
+    got = np.load(out)
+    whole = _OracleBand(G, E, 0, G, 0)
+    whole.iterate(2 * chunk)
+    ref = whole.stats()
+    nb = len(ref["hist"])
+    assert np.array_equal(got[:nb], ref["hist"])
+    assert list(got[nb:nb + 4]) == [ref["under"], ref["over"], ref["chaotic"], G * G]
+    assert got[nb + 4] == ref["dE_max"]
+    np.testing.assert_allclose(got[nb + 5:nb + 8], ref["p_mean"], rtol=1e-12)
+    np.testing.assert_allclose(got[nb + 8:nb + 11], ref["p_var"], rtol=1e-12)
