@@ -84,7 +84,7 @@ def parse():
     ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="scale of the batched config's step counts (1 = as configured)")
     ap.add_argument("--batch-precision", default="df64f", choices=["df64f", "fp32c", "df64"])
-    ap.add_argument("--batch-sample", type=int, default=512,
+    ap.add_argument("--batch-sample", type=int, default=1024,
                     help="cells per set run again in plain FP64 for the agreement figures")
     return ap.parse_args()
 
@@ -703,14 +703,17 @@ def batch_vs_fp64_sampled(b, sets, tuning, stream, device, barrier, per_set):
         eulp.close()
     l1 = float(np.abs(hist["batch"] / total - hist["fp64"] / total).sum())
     l1_self = float(np.abs(hist["fp64_ulp"] / total - hist["fp64"] / total).sum())
-    return {"cells": total, "per_set": per_set, "class_agreement": agree / total,
+    a, a_self = agree / total, agree_self / total
+    return {"cells": total, "per_set": per_set, "class_agreement": a,
             "worst_set_class_agreement": worst, "hist_l1": l1,
-            "fp64_vs_one_ulp_fp64": {"class_agreement": agree_self / total, "hist_l1": l1_self},
+            "fp64_vs_one_ulp_fp64": {"class_agreement": a_self, "hist_l1": l1_self},
             "chaotic_fraction_fp64": chaotic64 / total, "chaotic_fraction_batch": chaotic_b / total,
-            "meets_bar": bool(agree / total >= 0.995 and l1 <= 1e-2),
+            "meets_bar": bool(a >= 0.995 and l1 <= 1e-2),
+            "meets_intrinsic_bar": bool(a >= min(0.995, a_self - 0.005) and l1 <= max(1e-2, 2.0 * l1_self)),
             "fp64_map_steps": steps, "fp64_wall_s": wall,
-            "note": "bars: class agreement >= 0.995, hist L1 <= 1e-2 (the indicator-agreement bar); "
-                    "fp64_vs_one_ulp_fp64 is the level two FP64 runs reach"}
+            "note": "meets_bar: class agreement >= 0.995 and hist L1 <= 1e-2; meets_intrinsic_bar: within 0.5 % of "
+                    "and L1 <= max(1e-2, 2x) the level FP64 reaches against its own one-ulp-perturbed run "
+                    "(fp64_vs_one_ulp_fp64), the rule the tests use where chaotic cells decorrelate"}
 
 
 def long_horizon_leg(device, stream, barrier, G=256, E=40.0, S=1_000_000):
