@@ -93,3 +93,29 @@ def test_autotuner_picks_and_caches(tmp_path, monkeypatch, precision):
     assert best in cands
     assert tune.tune_batch(SETS, candidates=cands, precision=precision) == best      # from the cache
     assert (tmp_path / "cache.json").exists()
+
+
+@pytest.mark.parametrize("precision", ["df64f", "fp32c"])
+def test_batch_degenerate_sets_and_no_tangent(precision):
+    """Degenerate sets in one batch: a 1 x 1 grid, a set with zero steps (left
+    untouched), a ragged 3 x 3 grid, with the tangent off; each still equals its
+    single ensemble bit for bit, and the zero-step set keeps its initial state."""
+    from paper_1107_4107_b300.api import ArnoldBatch, ArnoldEnsemble
+    sets = [{"eps": 1.0, "h": 0.0628, "E": 400.0, "G": 1, "n_steps": 77, "seed": 11},
+            {"eps": 1.0, "h": 0.05, "E": 40.0, "G": 16, "n_steps": 0, "seed": 12},
+            {"eps": 1.0, "h": 0.1257, "E": 200000.0, "G": 3, "n_steps": 513, "seed": 13}]
+    b = ArnoldBatch(sets, tangent=False, precision=precision,
+                    tuning={"block_size": 64, "traj_per_thread": 1, "renorm_every": 50, "epoch_ms": 5})
+    b.init()
+    b.run()
+    b.sync()
+    assert b.info()["map_steps_per_run"] == 77 + 0 + 9 * 513
+    for k, q in enumerate(sets):
+        e = ArnoldEnsemble(q["G"] ** 2, eps=q["eps"], h=q["h"], precision=precision, tangent=False,
+                           renorm_every=50)
+        e.init_grid(q["G"], q["E"], seed=q["seed"])
+        if q["n_steps"]:
+            e.iterate(q["n_steps"])
+        for kind in ("X", "P", "dE_max"):
+            assert np.array_equal(b.indicator(k, kind), e.indicator(kind)), (k, kind)
+    assert np.array_equal(b.indicator(1, "dE_max"), np.zeros(256))
