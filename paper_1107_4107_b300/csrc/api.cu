@@ -27,7 +27,8 @@ static long double round_bits(long double x, int bits) {
 // rad) + d2 + d3; 2 pi split into c1 (14 bits) + c2 (16 bits) + c3, so k c1
 // and k c2 are exact for |k| < 256 turns.
 // DF64 table geometry (TabDF in step_df.cuh): D = 2 pi / 2048 split d1 (11
-// significant bits) + d2 + d3; 2 pi split as for the FP32 table.
+// significant bits) + d2 + d3; 2 pi split into c1 and c2 of 18 significant
+// bits each + c3, so k c1 and k c2 are exact for |k| < 64 turns.
 void df_tab(TabDF* tb) {
   const long double two_pi = 6.283185307179586476925286766559005768L;
   const long double D = two_pi / 2048.0L;

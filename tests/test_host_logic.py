@@ -264,3 +264,59 @@ def test_bench_banded_scan_on_two_gloo_ranks(tmp_path):
     assert got[nb + 4] == ref["dE_max"]
     np.testing.assert_allclose(got[nb + 5:nb + 8], ref["p_mean"], rtol=1e-12)
     np.testing.assert_allclose(got[nb + 8:nb + 11], ref["p_var"], rtol=1e-12)
+
+
+class _BlobEnsemble:
+    """Stand-in with the checkpoint calls of ArnoldEnsemble (host logic only)."""
+
+    def __init__(self, blob=b""):
+        self.blob = blob
+
+    def checkpoint(self):
+        return self.blob
+
+    def restore(self, blob):
+        self.blob = blob
+
+
+def test_fig4_checkpoint_is_one_atomic_file_checked_on_resume(tmp_path):
+    """The Fig. 4 runner's checkpoint holds state, window count and accumulated F
+    in one file written by rename; resuming checks F against the windows done
+    since the last snapshot boundary and refuses anything else."""
+    from paper_1107_4107_b300.experiments import _load_fig4_ckpt, _save_fig4_ckpt
+    path = str(tmp_path / "fig4.ckpt")
+    bounds, shape = [2, 10], (4, 8)
+    acc = np.zeros(shape, dtype=np.int64)
+    acc[1, 2] = 7
+    _save_fig4_ckpt(path, _BlobEnsemble(b"state-after-5-windows"), 5, acc)
+    assert sorted(os.listdir(tmp_path)) == ["fig4.ckpt"]          # no temporary left behind
+    e = _BlobEnsemble()
+    done, got = _load_fig4_ckpt(path, e, bounds, shape)
+    assert done == 5 and np.array_equal(got, acc) and e.blob == b"state-after-5-windows"
+    for bad_done, bad_acc, bad_shape in ((5, np.zeros(shape), shape),       # windows 3-5 missing from F
+                                         (2, acc, shape),                   # F not empty at a boundary
+                                         (5, acc, (8, 4))):                 # another F grid
+        _save_fig4_ckpt(path, _BlobEnsemble(b"x"), bad_done, np.asarray(bad_acc))
+        with pytest.raises(ValueError):
+            _load_fig4_ckpt(path, _BlobEnsemble(), bounds, bad_shape)
+    np.savez(path + ".npz", state=np.zeros(3, np.uint8))           # not a Fig. 4 checkpoint
+    with pytest.raises(ValueError):
+        _load_fig4_ckpt(path + ".npz", _BlobEnsemble(), bounds, shape)
+
+
+def test_tuner_candidates_per_precision():
+    from paper_1107_4107_b300 import tune
+    assert any(c["traj_per_thread"] == 2 for c in tune.candidates_for("fp32c"))
+    for prec in ("df64f", "df64"):
+        c = tune.candidates_for(prec)
+        assert c and all(x["traj_per_thread"] == 1 for x in c)
+
+
+def test_bench_workload_per_rank():
+    """Bands cover the scan's rows once (strong scaling); independent mode gives
+    every rank the whole grid with its own seed (weak scaling)."""
+    import bench
+    rows = [bench.rank_workload(4, r, "band", grid=2048) for r in range(4)]
+    assert [r0 for r0, _, _ in rows] == [0, 512, 1024, 1536] and {s for _, _, s in rows} == {0}
+    assert sum(n for _, n, _ in rows) == 2048
+    assert [bench.rank_workload(3, r, "independent", grid=2048) for r in range(3)] == [(0, 2048, r) for r in range(3)]
