@@ -217,6 +217,7 @@ class State:
         self.logsum = np.zeros(n)
         self.dE_max = np.zeros(n)
         self.e0 = energy(params.eps, self.X, self.P)
+        self.P0 = self.P.copy()
         self.V = np.zeros((3, n))
         self.megno = np.zeros((2, n)) if tangent else None   # (S, Ysum), see megno_mean()
         self.steps = 0
@@ -300,6 +301,11 @@ class State:
         if self.params.window > 0:
             return self.V.copy()
         return self.unwrapped_displacement() / self.time()
+
+    def velocity_deviation(self) -> np.ndarray:
+        """|V - P(0)|: Sec. IV reads a regular trajectory by its averaged velocity
+        staying close to its initial momentum vector; this is that distance."""
+        return np.sqrt(np.sum((self.velocity() - self.P0) ** 2, axis=0))
 
     def dE(self) -> np.ndarray:
         """Energy error |E(t) - E(0)| (Sec. III)."""

@@ -106,6 +106,26 @@ def test_invariant_subspaces_exact():
     assert np.all(st.X[2] == 0.0) and np.all(st.P[2] == 0.0)
 
 
+def test_velocity_deviation_closed_forms():
+    """|V - P(0)| (Sec. IV's reading of V): 0 at eps = 0, where V = P(0) exactly;
+    and for a pendulum trapped about x = pi on the invariant plane, whose x
+    stays within its amplitude of pi, V_x -> 0 like 2 amp / t while P(0) = (p0,
+    0, 0): |V - P(0)| -> |p0| within that bound.  Catches the momentum taken
+    at the end of the run instead of the start, and a wrong norm."""
+    X, P = _box(32, lo=(-20.0, -20.0, -20.0), hi=(20.0, 20.0, 20.0))
+    st = oracle.State(X, P, oracle.Params(eps=0.0, h=0.05), tangent=False).advance(300)
+    assert np.max(st.velocity_deviation()) < 1e-11
+    eps, p0 = 1.0, 0.5
+    X = np.zeros((3, 1)); X[0, 0] = math.pi + 0.3
+    P = np.zeros((3, 1)); P[0, 0] = p0
+    st = oracle.State(X, P, oracle.Params(eps=eps), tangent=False).advance(1000)
+    # energy p^2/2 + 2 eps cos x < 2 eps: trapped; amplitude from the energy
+    amp = math.acos(-(0.5 * p0 * p0 + 2.0 * eps * math.cos(math.pi + 0.3)) / (2.0 * eps))
+    t = st.time()
+    assert abs(abs(st.P[0, 0]) - p0) > 0.05              # |P(t)| is not |P(0)|: the reading needs P(0)
+    assert abs(st.velocity_deviation()[0] - p0) <= 2.0 * amp / t
+
+
 def test_pendulum_period_elliptic():
     """On the invariant plane H = p^2/2 + 2 eps cos x: a pendulum about x = pi with
     omega0^2 = 2 eps; period 4 K(k) / omega0, k = sin(amplitude / 2).  Catches a
