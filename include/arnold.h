@@ -96,6 +96,10 @@ extern "C" {
  * Needs a context created with megno = 1 (EINVAL otherwise). */
 #define ARNOLD_IND_MEGNO   11  /* [n] f64: mean MEGNO <Y>_m                                              */
 #define ARNOLD_IND_MEGNO_Y 12  /* [n] f64: MEGNO Y_m at the last renormalisation                         */
+/* The paper's own reading of V (Sec. IV): a regular trajectory's averaged
+ * velocity stays close to its initial momentum vector, a chaotic one's wanders
+ * off; |V - P(0)| puts a number on it beside chi. */
+#define ARNOLD_IND_VDEV    13  /* [n] f64: |V - P(t=0)|, V as ARNOLD_IND_V                                */
 
 /* ---- parameters ------------------------------------------------------------ */
 typedef struct arnold_params {
@@ -195,7 +199,8 @@ int arnold_init_gaussian(arnold_ctx* ctx, double E, double px0, double py0, doub
  * area are dropped): from now on, every renorm_every steps, a trajectory whose
  * momentum direction (cos theta = p_z/|P|, phi = atan2(p_y, p_x) in [0, 2pi))
  * is outside [cos_lo, cos_hi] x [phi_lo, phi_hi] is flagged (ARNOLD_IND_LEFT).
- * Flags reset at set_state / init_grid / this call.  Errors: EINVAL, ENOMEM. */
+ * Flags reset at set_state, init_grid, init_sphere, init_gaussian and this
+ * call.  Errors: EINVAL, ENOMEM. */
 int arnold_track_patch(arnold_ctx* ctx, double cos_lo, double cos_hi, double phi_lo, double phi_hi);
 
 /* Snapshots of V (Sec. IV: one F per window Delta t): while enabled, the kernel
@@ -368,8 +373,8 @@ void arnold_batch_destroy(arnold_batch* b);
 
 /* ---- checkpoint / resume ----------------------------------------------------
  * The complete per-trajectory state (phase-space state, tangent, laps, window
- * references, log sums, energy references and maxima, V, MEGNO sums when
- * enabled, area-tracking flags when tracking is on) plus the step counter, so
+ * references, log sums, energy references and maxima, V, initial momenta, MEGNO
+ * sums when enabled, area-tracking flags when tracking is on) plus the step counter, so
  * that a run resumed from a checkpoint continues bit for bit as if
  * uninterrupted (the paper's 24 h runs, Sec. IV, motivate it).  Layout: a
  * 128-byte header (magic "ARNOLDC2", precision, tangent, n, steps, scheme,

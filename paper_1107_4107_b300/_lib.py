@@ -16,9 +16,9 @@ SCHEMES = {"yoshida6a": 0, "triplejump6": 1, "leapfrog2": 2}
 PRECISIONS = {"fp64": 0, "fp32c": 1, "df64": 2, "df64f": 3}
 HOST, DEVICE = 0, 1
 IND = {"chi": 0, "V": 1, "dE": 2, "dE_max": 3, "class": 4, "X": 5, "P": 6, "dX": 7, "tangent": 8, "logsum": 9,
-       "left": 10, "megno": 11, "megno_y": 12}
+       "left": 10, "megno": 11, "megno_y": 12, "vdev": 13}
 IND_SHAPE = {"chi": 1, "V": 3, "dE": 1, "dE_max": 1, "class": 1, "X": 3, "P": 3, "dX": 3, "tangent": 6, "logsum": 1,
-             "left": 1, "megno": 1, "megno_y": 1}
+             "left": 1, "megno": 1, "megno_y": 1, "vdev": 1}
 SHELL_DIRECTION, SHELL_PZ = 1, 2
 HIST_BINS = 200
 NOALLOC_MAX_N = 1 << 40

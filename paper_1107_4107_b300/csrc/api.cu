@@ -255,7 +255,7 @@ void free_all(arnold_ctx* c) {
   void* ptrs[] = {c->s.st, c->s.tg, c->s.lap, c->s.lapref, c->s.ref, c->s.logsum, c->s.demax, c->s.e0, c->s.V,
                   c->f.hi, c->f.lo, c->f.tg, c->sc, c->th, c->scf, c->scd, c->flags, c->partials, c->stats_out,
                   c->scratch, c->scratch2, c->ck, c->seg, c->lam, c->lamf, c->gh, c->ge, c->sum_part, c->s.left,
-                  c->vhist, c->s.megno, c->f.tg_lo, c->draw};
+                  c->vhist, c->s.megno, c->f.tg_lo, c->draw, c->s.p0};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -325,7 +325,7 @@ int read_indicator(arnold_ctx* c, int kind, void* dst) {
 size_t indicator_bytes(int kind, long long n) {
   switch (kind) {
     case ARNOLD_IND_CHI: case ARNOLD_IND_DE: case ARNOLD_IND_DE_MAX: case ARNOLD_IND_LOGSUM:
-    case ARNOLD_IND_MEGNO: case ARNOLD_IND_MEGNO_Y: return 8 * (size_t)n;
+    case ARNOLD_IND_MEGNO: case ARNOLD_IND_MEGNO_Y: case ARNOLD_IND_VDEV: return 8 * (size_t)n;
     case ARNOLD_IND_CLASS: case ARNOLD_IND_LEFT: return (size_t)n;
     case ARNOLD_IND_V: case ARNOLD_IND_X: case ARNOLD_IND_P: case ARNOLD_IND_DX: return 24 * (size_t)n;
     case ARNOLD_IND_TANGENT: return 48 * (size_t)n;
@@ -425,6 +425,7 @@ int arnold_create(const arnold_params* prm, int64_t n_traj, int device, void* cu
   if (e == cudaSuccess) e = dalloc(&c->s.demax, n);
   if (e == cudaSuccess) e = dalloc(&c->s.e0, n);
   if (e == cudaSuccess) e = dalloc(&c->s.V, 3 * n);
+  if (e == cudaSuccess) e = dalloc(&c->s.p0, 3 * n);
   if (e == cudaSuccess) e = dalloc(&c->flags, 1);
   if (e == cudaSuccess) e = cudaMemset(c->flags, 0, sizeof(int));
   c->stats_grid = c->sms * 4;
@@ -944,6 +945,7 @@ static int ckpt_arrays(const arnold_ctx* c, void** ptrs, size_t* sizes) {
   add(c->s.demax, 8 * n);
   add(c->s.e0, 8 * n);
   add(c->s.V, 24 * n);
+  add(c->s.p0, 24 * n);
   add(c->s.megno, 16 * n);
   add(c->s.left, n);
   return k;

@@ -56,6 +56,7 @@ struct Fp64State {
   double* demax;   // [n]
   double* e0;      // [n] H at t = 0
   double* V;       // [3][n] V (x, y, z components) of the last closed window
+  double* p0;      // [3][n] momenta p_x, p_y, p_z at t = 0 (for |V - P(0)|)
   unsigned char* left;  // [n] area tracking: 1 once the momentum direction left the patch (null = off)
   double patch[4];      // cos_lo, cos_hi, phi_lo, phi_hi of the tracked patch
   double* megno;        // [2][n] MEGNO sums S = sum_j j l_j and Ysum = sum_j Y_j (null = off)

@@ -59,6 +59,7 @@ __device__ __forceinline__ void init_common(const InitArgs& a, long long i, doub
   a.s.lapref[i] = lu; a.s.lapref[n + i] = lv; a.s.lapref[2 * n + i] = lz;
   a.s.ref[i] = u; a.s.ref[n + i] = v; a.s.ref[2 * n + i] = z;
   a.s.e0[i] = e0;
+  a.s.p0[i] = 0.5 * (qu + qv); a.s.p0[n + i] = 0.5 * (qu - qv); a.s.p0[2 * n + i] = pz;
   a.s.demax[i] = 0.0;
   if (a.s.logsum) a.s.logsum[i] = 0.0;
   if (a.s.megno) { a.s.megno[i] = 0.0; a.s.megno[n + i] = 0.0; }
@@ -351,19 +352,25 @@ __device__ __forceinline__ void indicator_one(const ReadArgs& a, long long i, do
       v[2] = pz;
       break;
     case ARNOLD_IND_DX:
-    case ARNOLD_IND_V: {
-      if (a.kind == ARNOLD_IND_V && a.W > 0) {
+    case ARNOLD_IND_V:
+    case ARNOLD_IND_VDEV: {
+      if (a.kind != ARNOLD_IND_DX && a.W > 0) {
         v[0] = a.s.V[i]; v[1] = a.s.V[n + i]; v[2] = a.s.V[2 * n + i];
-        break;
+      } else {
+        load_state();
+        const double dU = (u - a.s.ref[i]) + kTwoPi * (double)(lu - a.s.lapref[i]);
+        const double dV = (vv - a.s.ref[n + i]) + kTwoPi * (double)(lv - a.s.lapref[n + i]);
+        const double dZ = (z - a.s.ref[2 * n + i]) + kTwoPi * (double)(lz - a.s.lapref[2 * n + i]);
+        const double sc = a.kind == ARNOLD_IND_DX ? 1.0 : 1.0 / a.t;
+        v[0] = 0.5 * (dU + dV) * sc;
+        v[1] = 0.5 * (dU - dV) * sc;
+        v[2] = dZ * sc;
       }
-      load_state();
-      const double dU = (u - a.s.ref[i]) + kTwoPi * (double)(lu - a.s.lapref[i]);
-      const double dV = (vv - a.s.ref[n + i]) + kTwoPi * (double)(lv - a.s.lapref[n + i]);
-      const double dZ = (z - a.s.ref[2 * n + i]) + kTwoPi * (double)(lz - a.s.lapref[2 * n + i]);
-      const double sc = a.kind == ARNOLD_IND_V ? 1.0 / a.t : 1.0;
-      v[0] = 0.5 * (dU + dV) * sc;
-      v[1] = 0.5 * (dU - dV) * sc;
-      v[2] = dZ * sc;
+      if (a.kind == ARNOLD_IND_VDEV) {   // |V - P(0)|: regular cells keep V near their initial momentum
+        const double ex = v[0] - a.s.p0[i], ey = v[1] - a.s.p0[n + i], ez = v[2] - a.s.p0[2 * n + i];
+        v[0] = sqrt(ex * ex + ey * ey + ez * ez);
+        v[1] = v[2] = 0.0;
+      }
       break;
     }
     case ARNOLD_IND_TANGENT: {

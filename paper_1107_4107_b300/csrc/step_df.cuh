@@ -44,24 +44,6 @@ __device__ __forceinline__ Pair df_mul_u(const Pair& a, const Pair& b) {
   return r;
 }
 
-__device__ __forceinline__ Pair df_sqr(const Pair& a) {
-  const float p = __fmul_rn(a.hi, a.hi);
-  float e = fmaf(a.hi, a.hi, -p);
-  e = fmaf(2.0f * a.hi, a.lo, e);
-  Pair r;
-  fast_two_sum(p, e, r.hi, r.lo);
-  return r;
-}
-
-__device__ __forceinline__ Pair df_add(const Pair& a, const Pair& b) {
-  float s, e;
-  two_sum(a.hi, b.hi, s, e);
-  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
-  Pair r;
-  fast_two_sum(s, e, r.hi, r.lo);
-  return r;
-}
-
 // a + b without the final renormalisation: (s, e) with |e| up to ~ulp(s), for
 // sums that only feed products (df_mul_u multiplies both words, so an
 // unnormalised low word costs no accuracy there).

@@ -204,9 +204,16 @@ def scan_agreement(E: float = 400.0, steps: int = 1_000_000, G: int = 2048,
         b.synchronize()
         e.sync()
         chi, cls = e.indicator("chi"), e.indicator("class")
+        dev = e.indicator("vdev")
+        rank = lambda v: np.argsort(np.argsort(v)).astype(np.float64)  # noqa: E731
         r = {"precision": prec, "E": E, "G": G, "steps": steps, "seconds": a.elapsed_time(b) * 1e-3,
              "map_steps_per_s": G * G * steps / (a.elapsed_time(b) * 1e-3), "chaotic_fraction": float(cls.mean()),
-             "dE_max": float(e.indicator("dE_max").max())}
+             "dE_max": float(e.indicator("dE_max").max()),
+             # Sec. IV's reading of V beside chi: |V - P(0)| of chaotic vs regular cells, and its rank
+             # correlation with chi (reported)
+             "vdev_median_chaotic": float(np.median(dev[cls == 1])) if cls.any() else None,
+             "vdev_median_regular": float(np.median(dev[cls == 0])) if (cls == 0).any() else None,
+             "vdev_chi_rank_correlation": float(np.corrcoef(rank(dev), rank(chi))[0, 1])}
         if ref is None:
             ref = (chi, cls)
         else:

@@ -344,3 +344,37 @@ def test_oracle_scale_scan_paper_moderate_E15(torch_cuda):
           f"{a_own:.5f}, L1 {l1_own:.2e}; chaotic {ref_cls.mean():.4f}")
     assert a_gpu >= a_own - 0.005
     assert l1_gpu <= max(1e-2, 2.0 * l1_own)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL), ("df64f", 1e-9), ("fp32c", 3e-7)])
+@pytest.mark.parametrize("window", [0, 30])
+def test_velocity_deviation_parity(torch_cuda, precision, tol, window):
+    """|V - P(0)| (ARNOLD_IND_VDEV) against the oracle's, 100 steps, every cell of a
+    ragged box ensemble, with V over the whole run and over 30-step windows; the
+    bar is each mode's 100-step bar (the FP64 one, DF64F's, FP32C's)."""
+    n = 1001
+    X, P = inputs.box(n, seed=31)
+    st = oracle.State(X, P, oracle_params(R=10, window=window)).advance(100)
+    ens = _ens(n, precision=precision, renorm_every=10, window=window)
+    ens.set_state(X, P)
+    ens.iterate(100)
+    assert rel_err(ens.indicator("vdev"), st.velocity_deviation()) < tol
+    ens.sync()
+
+
+def test_velocity_deviation_separates_chaotic_cells(torch_cuda):
+    """Sec. IV reads the web by V: regular trajectories keep V near their initial
+    momentum, chaotic ones drift.  On the 128 x 128 scan at E = 40 after 1e4
+    steps, |V - P(0)| of the cells chi calls chaotic exceeds that of the regular
+    ones (medians), and the rank correlation of |V - P(0)| with chi is reported."""
+    G, E = 128, 40.0
+    ens = _ens(G * G)
+    ens.init_grid(G, E)
+    ens.iterate(10000)
+    d, chi, cls = ens.indicator("vdev"), ens.indicator("chi"), ens.indicator("class").astype(bool)
+    rank = lambda a: np.argsort(np.argsort(a)).astype(np.float64)  # noqa: E731
+    rho = float(np.corrcoef(rank(d), rank(chi))[0, 1])
+    print(f"E={E}: chaotic {cls.mean():.4f}, median |V-P0| chaotic {np.median(d[cls]):.3e} regular "
+          f"{np.median(d[~cls]):.3e}, Spearman rank correlation with chi {rho:.3f}")
+    assert cls.sum() >= 5
+    assert np.median(d[cls]) > np.median(d[~cls])
