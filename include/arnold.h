@@ -191,7 +191,8 @@ int arnold_init_sphere(arnold_ctx* ctx, double E, uint64_t seed, int64_t offset,
  * candidates examined up to the last one kept.  Synchronises the stream.
  * Uses ~0.8 MB of library-owned device scratch (allocated on first use).
  * Errors: EINVAL (offset < 0, sigma < 0, non-finite input), ERANGE (fewer than
- * n real p_z among the first 64 n + 2^24 candidates), ENOMEM, ECUDA. */
+ * n real p_z among the first 64 n + 2^24 candidates; the trajectories are then
+ * only partly set and must be initialised again), ENOMEM, ECUDA. */
 int arnold_init_gaussian(arnold_ctx* ctx, double E, double px0, double py0, double sigma, uint64_t seed,
                          int64_t offset, int64_t* n_drawn);
 
