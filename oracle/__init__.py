@@ -358,7 +358,7 @@ def stats(chi: np.ndarray, dE: np.ndarray, P: np.ndarray, t: float, kappa: float
     }
 
 
-# ---- gradient reference for the adjoint (BASELINE pattern: differentiation) ----
+# ---- gradient reference for the adjoint (derivatives of the N-step map) ----
 def loss_variance(P: np.ndarray) -> float:
     """L = (1/3) sum_alpha Var_i P_alpha^i (population variance)."""
     return float(np.mean(np.var(P, axis=1)))

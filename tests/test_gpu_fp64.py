@@ -1,6 +1,6 @@
 """FP64 CUDA path vs the FP64 oracle (element by element, same seeded inputs).
 
-Tolerance (BASELINE: <= 1e-12 per-step relative error in FP64): both sides
+Tolerance (the FP64 path's stated bar, <= 1e-12 per-step relative error): both sides
 are FP64; they differ by FMA contraction, the sincos implementation (CUDA
 table method vs libm, ~1 ulp) and the rotated coordinates used on the GPU
 (u = x + y, v = x - y), i.e. by rounding only.  Errors are measured as
