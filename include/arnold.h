@@ -63,7 +63,9 @@ extern "C" {
 #define ARNOLD_FP64  0  /* state, tangent and sincos to FP64 accuracy (the paper used double precision,
                            Sec. III); FP64 instructions only where that accuracy needs them             */
 #define ARNOLD_FP32C 1  /* compensated FP32: float-pair angles (held in a [1024, 2048) rad window, whole
-                           turns removed exactly) and momenta, two-sum updates; FP64 logs and energy     */
+                           turns removed exactly) and momenta, two-sum updates; FP64 logs and energy.
+                           Forces and tangent in FP32: a short-horizon mode (its chi field holds the
+                           scan's agreement bar to ~1e4 steps, not to 1e6).                             */
 #define ARNOLD_DF64  2  /* double-float: state, kicks and tangent in float pairs (~48-bit), FP64-grade
                            trajectories on the FP32 pipes.  No adjoint.                                 */
 #define ARNOLD_DF64F 3  /* DF64 with a faster sincos: the same double-float state, products, sums and

@@ -41,9 +41,11 @@ def _ptr_kind(a):
 class ArnoldEnsemble:
     """n independent trajectories held on one GPU (library-owned device memory).
 
-    precision: "fp64" (FP64 accuracy), "fp32c" (compensated FP32, FP32 tangent),
-    "df64" (double-float state, kicks and tangent) or "df64f" (double-float with
-    a ~3e-10 sincos); scheme: "yoshida6a", "triplejump6" or "leapfrog2"."""
+    precision: "fp64" (FP64 accuracy), "df64f" (double-float state, kicks and
+    tangent with a ~3e-10 sincos on the FP32 pipes: the compensated mode for
+    long runs), "df64" (the same with an accurate sincos) or "fp32c"
+    (compensated state updates, FP32 forces and tangent: short horizons);
+    scheme: "yoshida6a", "triplejump6" or "leapfrog2"."""
 
     def __init__(self, n: int, eps: float = 1.0, h: float | None = None, scheme: str = "yoshida6a",
                  precision: str = "fp64", tangent: bool = True, renorm_every: int = 100, window: int = 0,
