@@ -320,3 +320,28 @@ def test_bench_workload_per_rank():
     assert [r0 for r0, _, _ in rows] == [0, 512, 1024, 1536] and {s for _, _, s in rows} == {0}
     assert sum(n for _, n, _ in rows) == 2048
     assert [bench.rank_workload(3, r, "independent", grid=2048) for r in range(3)] == [(0, 2048, r) for r in range(3)]
+
+
+def test_long_horizon_oracle_records_describe_the_sampled_cells():
+    """The oracle's 1e6-step records (tests/golden/oracle_scan_2048_1e6*.json)
+    hold, for every energy the GPU test compares, chi at every mark on exactly
+    the cells the seeded sampler draws; the one-ulp record has the same cells."""
+    import hashlib
+    import json
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    with open(os.path.join(here, "oracle_scan_2048_1e6.json")) as f:
+        g = json.load(f)
+    with open(os.path.join(here, "oracle_scan_2048_1e6_ulp.json")) as f:
+        u = json.load(f)
+    idx = inputs.sample_cells(g["grid"] ** 2, g["cells"], seed=g["sample_seed"])
+    assert hashlib.sha256(idx.astype("<i8").tobytes()).hexdigest() == g["cells_sha256"]
+    for key in ("grid", "eps", "h", "renorm_every", "seed", "sample_seed", "cells", "cells_sha256", "marks"):
+        assert u[key] == g[key], key
+    assert set(g["energies"]) == {"400", "40", "15"}
+    assert set(u["energies"]) == {"40", "15"}
+    for rec in (g, u):
+        for row in rec["energies"].values():
+            assert set(row["chi"]) == {str(m) for m in g["marks"]}
+            for chi in row["chi"].values():
+                chi = np.asarray(chi)
+                assert chi.shape == (g["cells"],) and np.all(np.isfinite(chi)) and np.all(chi > 0)
