@@ -190,13 +190,34 @@ def scan_agreement(E: float = 400.0, steps: int = 1_000_000, G: int = 2048,
     """The Arnold-web scan of Sec. IV on a G x G grid of initial actions at
     energy E, run to `steps` steps in every precision mode from the same initial
     conditions; per mode the time, chaotic fraction and, against the first mode,
-    class agreement and the L1 distance of the log10 chi histograms."""
+    class agreement and the L1 distance of the log10 chi histograms.
+
+    "fp64ulp" is FP64 from the grid's angles moved up by one ulp (p_z again
+    from the energy; z moves by exactly one ulp, x and y through the rotated
+    angles u = x + y, v = x - y at their rounding): against "fp64" it gives the
+    agreement any two runs that round differently can reach on this field."""
+    return list(iter_scan_agreement(E, steps, G, precisions, seed, device))
+
+
+def iter_scan_agreement(E: float = 400.0, steps: int = 1_000_000, G: int = 2048,
+                        precisions=("fp64", "fp32c", "df64", "df64f"), seed: int = 0, device: int = 0):
+    """scan_agreement, one mode's record at a time as each run finishes."""
     import torch
     st = torch.cuda.current_stream(device)
-    out, ref = [], None
+    ref = None
     for prec in precisions:
-        e = ArnoldEnsemble(G * G, precision=prec, device=device, stream=st.cuda_stream)
-        e.init_grid(G, E, seed=seed)
+        e = ArnoldEnsemble(G * G, precision="fp64" if prec == "fp64ulp" else prec, device=device,
+                           stream=st.cuda_stream)
+        if prec == "fp64ulp":
+            raw = torch.empty((6, G * G), dtype=torch.float64, device=f"cuda:{device}")
+            e.init_grid(G, E, seed=seed, raw_out=raw)
+            st.synchronize()
+            X = torch.nextafter(raw[:3], torch.full_like(raw[:3], math.inf)).contiguous()
+            e.set_state_shell(X, raw[3:].contiguous(), 2, E)
+            st.synchronize()
+            del raw, X
+        else:
+            e.init_grid(G, E, seed=seed)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(st)
         e.iterate(steps)
@@ -221,8 +242,7 @@ def scan_agreement(E: float = 400.0, steps: int = 1_000_000, G: int = 2048,
             r["class_agreement"] = float(np.mean(cls == ref[1]))
             r["hist_l1"] = float(np.abs(h(chi) - h(ref[0])).sum())
         e.close()
-        out.append(r)
-    return out
+        yield r
 
 
 def timed_diffusion_rate(n: int = 32000, E: float = 15.0, steps: int = 50000, precision: str = "fp64",
@@ -265,8 +285,8 @@ def main(argv=None):
     args = sys.argv[1:] if argv is None else argv
     if args and args[0] == "scan" and len(args) >= 3:
         precs = tuple(args[4].split(",")) if len(args) > 4 else ("fp64", "fp32c", "df64", "df64f")
-        for r in scan_agreement(E=float(args[1]), steps=int(float(args[2])),
-                                G=int(args[3]) if len(args) > 3 else 2048, precisions=precs):
+        for r in iter_scan_agreement(E=float(args[1]), steps=int(float(args[2])),
+                                     G=int(args[3]) if len(args) > 3 else 2048, precisions=precs):
             print(json.dumps(r), flush=True)
         return
     if args and args[0] == "fig4" and len(args) >= 3:

@@ -49,6 +49,41 @@ def test_scan_agreement_runs_all_modes_from_the_same_ics():
     assert all(r["map_steps_per_s"] > 0 for r in rows)
 
 
+def test_scan_one_ulp_fp64_arm():
+    """The "fp64ulp" arm of the scan: FP64 from the grid's angles moved up by one
+    ulp, p_z again from the energy (the same perturbation as the oracle's one-ulp
+    record).  Over a short horizon its classes agree with FP64's, and it starts
+    from a moved state on the energy shell."""
+    import torch
+
+    import oracle
+    from paper_1107_4107_b300.api import ArnoldEnsemble
+    from paper_1107_4107_b300.experiments import scan_agreement
+    rows = scan_agreement(E=15.0, steps=300, G=64, precisions=("fp64", "fp64ulp"))
+    assert [r["precision"] for r in rows] == ["fp64", "fp64ulp"]
+    assert rows[1]["class_agreement"] >= 0.99 and rows[1]["hist_l1"] <= 1e-2
+    G, E = 64, 15.0
+    raw = torch.empty((6, G * G), dtype=torch.float64, device="cuda:0")
+    a = ArnoldEnsemble(G * G, precision="fp64")
+    a.init_grid(G, E, raw_out=raw)
+    a.sync()
+    X = torch.nextafter(raw[:3], torch.full_like(raw[:3], math.inf)).contiguous()
+    b = ArnoldEnsemble(G * G, precision="fp64")
+    b.set_state_shell(X, raw[3:].contiguous(), 2, E)
+    b.sync()
+    Xa, Pa = a.indicator("X"), a.indicator("P")
+    Xb, Pb = b.indicator("X"), b.indicator("P")
+    # z is stored as given; x and y come back through the rotated angles
+    # u = x + y, v = x - y, so only to their rounding
+    assert np.array_equal(Xb[2], np.nextafter(Xa[2], np.inf))
+    assert np.max(np.abs(Xb[:2] - Xa[:2])) < 4e-15
+    assert np.array_equal(Pb[:2], Pa[:2])
+    assert np.max(np.abs(Pb[2] - Pa[2])) < 1e-12
+    assert np.max(np.abs(oracle.energy(1.0, Xb, Pb) - E)) < 1e-12
+    a.close()
+    b.close()
+
+
 def test_diffusion_resume_rejects_an_inconsistent_checkpoint(tmp_path):
     """A checkpoint whose accumulated F does not hold the windows since the last
     snapshot boundary of the resumed schedule is refused, not silently used."""
