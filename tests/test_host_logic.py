@@ -345,3 +345,26 @@ def test_long_horizon_oracle_records_describe_the_sampled_cells():
             for chi in row["chi"].values():
                 chi = np.asarray(chi)
                 assert chi.shape == (g["cells"],) and np.all(np.isfinite(chi)) and np.all(chi > 0)
+
+
+def test_long_horizon_record_merge_refuses_other_cells(tmp_path):
+    """make_oracle_scan_1e6.py --energy adds an energy to an existing record
+    only if that record describes the same grid, cells and marks."""
+    import importlib.util
+    import json
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "make_oracle_scan_1e6.py")
+    spec = importlib.util.spec_from_file_location("make_oracle_scan_1e6", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    base = {"grid": 2048, "eps": 1.0, "h": 0.1, "renorm_every": 100, "scheme": "yoshida6a", "seed": 0,
+            "sample_seed": 2048, "cells": 4, "cells_sha256": "abc", "marks": [10, 100], "energies": {}}
+    out = str(tmp_path / "rec.json")
+    assert mod._merge_base(dict(base), out) == base            # nothing stored yet: the new record
+    stored = dict(base, energies={"400": {"chi": {}}})
+    with open(out, "w") as f:
+        json.dump(stored, f)
+    assert mod._merge_base(dict(base), out)["energies"] == {"400": {"chi": {}}}
+    with pytest.raises(SystemExit):
+        mod._merge_base(dict(base, cells_sha256="def"), out)
+    with pytest.raises(SystemExit):
+        mod._merge_base(dict(base, marks=[10, 1000]), out)
