@@ -38,6 +38,28 @@ def _ptr_kind(a):
     return ctypes.c_void_p(a.ctypes.data), _lib.HOST
 
 
+def _dtype_name(a) -> str:
+    return str(a.dtype).split(".")[-1]
+
+
+def _buf(a, count: int, dtypes, what: str, device: int, kind=None):
+    """(pointer, ptr_kind) of a caller buffer that the library reads or writes
+    as `count` elements of one of `dtypes`, checked first: the C ABI takes bare
+    pointers, so a short, mistyped or foreign-device buffer would be accessed
+    out of bounds.  A torch CUDA tensor must live on the context's `device`;
+    kind (_lib.HOST or _lib.DEVICE) is required where the call fixes it."""
+    p, k = _ptr_kind(a)
+    n = a.numel() if _is_torch(a) else a.size
+    if n != count or _dtype_name(a) not in dtypes:
+        raise ValueError(f"{what}: expected {count} elements of {'/'.join(dtypes)}, "
+                         f"got {n} of {_dtype_name(a)}")
+    if k == _lib.DEVICE and a.device.index != device:
+        raise ValueError(f"{what}: tensor is on cuda:{a.device.index}, the context on cuda:{device}")
+    if kind is not None and k != kind:
+        raise ValueError(f"{what} must be {'device' if kind == _lib.DEVICE else 'host'} memory")
+    return p, k
+
+
 class ArnoldEnsemble:
     """n independent trajectories held on one GPU (library-owned device memory).
 
@@ -102,18 +124,22 @@ class ArnoldEnsemble:
         for a, rows in ((X, 3), (P, 3), (W, 6)):
             if a is not None and (tuple(a.shape) != (rows, self.n) or str(a.dtype).split(".")[-1] != "float64"):
                 raise ValueError(f"expected float64 [{rows}][{self.n}]")
+            if a is not None:
+                _buf(a, rows * self.n, ("float64",), "set_state", self.device)
         check(_lib.lib().arnold_set_state(self._h, px, pp, pw, kx), "arnold_set_state")
 
     def init_grid(self, G: int, E: float, seed: int = 0, row0: int = 0, raw_out=None):
-        """Grid-slice initial conditions generated on the device (Sec. IV)."""
-        pr, _ = _ptr_kind(raw_out)
+        """Grid-slice initial conditions generated on the device (Sec. IV);
+        raw_out: None or a CUDA float64 tensor [6][n] for the generated X, P."""
+        pr = None if raw_out is None else \
+            _buf(raw_out, 6 * self.n, ("float64",), "raw_out", self.device, _lib.DEVICE)[0]
         check(_lib.lib().arnold_init_grid(self._h, G, row0, E, seed, pr), "arnold_init_grid")
 
     def set_state_shell(self, X, Pdir, mode: int, E: float):
         """Fixed-energy initial momenta (Sec. IV): mode 1 scales unit directions
         Pdir to the shell, mode 2 takes (p_x, p_y) and sets p_z from the energy."""
-        px, kx = _ptr_kind(X)
-        pp, kp = _ptr_kind(Pdir)
+        px, kx = _buf(X, 3 * self.n, ("float64",), "X", self.device)
+        pp, kp = _buf(Pdir, 3 * self.n, ("float64",), "P", self.device)
         if kx != kp:
             raise ValueError("X and P must both be host or both device")
         check(_lib.lib().arnold_set_state_shell(self._h, px, pp, int(mode), float(E), kx), "arnold_set_state_shell")
@@ -144,7 +170,7 @@ class ArnoldEnsemble:
         """Counts of the direction of V on the momentum sphere (F of Sec. IV)."""
         if out is None:
             out = np.zeros((n_cos, n_phi), dtype=np.uint64)
-        po, ko = _ptr_kind(out)
+        po, ko = _buf(out, int(n_cos) * int(n_phi), ("uint64", "int64"), "histogram", self.device)
         check(_lib.lib().arnold_velocity_histogram(self._h, n_cos, n_phi, *[float(v) for v in patch], int(filtered), po,
                                                    ko, int(accumulate)), "arnold_velocity_histogram")
         return out
@@ -187,10 +213,10 @@ class ArnoldEnsemble:
         """Indicator `kind` (see _lib.IND) into `out` (numpy host array, torch CUDA
         tensor) or a new numpy array."""
         rows = _lib.IND_SHAPE[kind]
+        dtype = np.uint8 if kind in ("class", "left") else np.float64
         if out is None:
-            dtype = np.uint8 if kind in ("class", "left") else np.float64
             out = np.empty((rows, self.n) if rows > 1 else (self.n,), dtype=dtype)
-        po, ko = _ptr_kind(out)
+        po, ko = _buf(out, rows * self.n, (np.dtype(dtype).name,), f"indicator({kind})", self.device)
         check(_lib.lib().arnold_indicator(self._h, _lib.IND[kind], po, ko), f"arnold_indicator({kind})")
         return out
 
@@ -202,10 +228,11 @@ class ArnoldEnsemble:
     def stats_arrays(self, chi, dE, P, t: float, kappa: float = 10.0) -> dict:
         """Statistics of caller device arrays (torch CUDA float64)."""
         s = _lib.Stats()
-        pc, _ = _ptr_kind(chi)
-        pd, _ = _ptr_kind(dE)
-        pp, _ = _ptr_kind(P)
-        check(_lib.lib().arnold_stats_arrays(self._h, int(chi.shape[0]), pc, pd, pp, t, kappa, ctypes.byref(s)),
+        n = int(chi.shape[0])
+        pc, _ = _buf(chi, n, ("float64",), "chi", self.device, _lib.DEVICE)
+        pd, _ = _buf(dE, n, ("float64",), "dE", self.device, _lib.DEVICE)
+        pp, _ = _buf(P, 3 * n, ("float64",), "P", self.device, _lib.DEVICE)
+        check(_lib.lib().arnold_stats_arrays(self._h, n, pc, pd, pp, t, kappa, ctypes.byref(s)),
               "arnold_stats_arrays")
         return stats_dict(s)
 
@@ -250,12 +277,15 @@ class ArnoldEnsemble:
             out_x = np.empty((3, self.n)) if out_x is None else out_x
             out_p = np.empty((3, self.n)) if out_p is None else out_p
             gpar = np.empty(2)
-        px, k = _ptr_kind(dL_dx) if dL_dx is not None else (None, None)
-        pp, k2 = _ptr_kind(dL_dp) if dL_dp is not None else (None, None)
+        c3 = 3 * self.n
+        px, k = _buf(dL_dx, c3, ("float64",), "dL_dx", self.device) if dL_dx is not None else (None, None)
+        pp, k2 = _buf(dL_dp, c3, ("float64",), "dL_dp", self.device) if dL_dp is not None else (None, None)
         kind = k if k is not None else k2
-        ox, _ = _ptr_kind(out_x)
-        op, _ = _ptr_kind(out_p)
-        og, _ = _ptr_kind(gpar)
+        if k is not None and k2 is not None and k != k2:
+            raise ValueError("dL_dx and dL_dp must both be host or both device")
+        ox, _ = _buf(out_x, c3, ("float64",), "out_x", self.device, kind)
+        op, _ = _buf(out_p, c3, ("float64",), "out_p", self.device, kind)
+        og, _ = _buf(gpar, 2, ("float64",), "gpar", self.device, kind)
         check(_lib.lib().arnold_grad(self._h, px, pp, ox, op, og, kind), "arnold_grad")
         return out_x, out_p, gpar[0], gpar[1]
 
@@ -357,6 +387,7 @@ class ArnoldBatch:
                                     int(bool(tangent)), ctypes.byref(tu), device, ctypes.c_void_p(stream),
                                     ctypes.byref(h)), "arnold_batch_create")
         self._h = h
+        self.device = device
         self.precision = precision
         self.sets = [dict(q) for q in sets]
         self.tuning = {f: getattr(tu, f) for f, _ in _lib.BatchTuning._fields_}
@@ -395,9 +426,10 @@ class ArnoldBatch:
         q = self.sets[set_index]
         n = int(q["G"]) ** 2
         rows = _lib.IND_SHAPE[kind]
+        dtype = np.uint8 if kind in ("class", "left") else np.float64
         if out is None:
-            out = np.empty((rows, n) if rows > 1 else (n,), dtype=np.uint8 if kind == "class" else np.float64)
-        po, ko = _ptr_kind(out)
+            out = np.empty((rows, n) if rows > 1 else (n,), dtype=dtype)
+        po, ko = _buf(out, rows * n, (np.dtype(dtype).name,), f"indicator({kind})", self.device)
         check(_lib.lib().arnold_batch_indicator(self._h, set_index, _lib.IND[kind], po, ko), "arnold_batch_indicator")
         return out
 

@@ -368,3 +368,50 @@ def test_long_horizon_record_merge_refuses_other_cells(tmp_path):
         mod._merge_base(dict(base, cells_sha256="def"), out)
     with pytest.raises(SystemExit):
         mod._merge_base(dict(base, marks=[10, 1000]), out)
+
+
+def test_binding_checks_caller_buffers_before_the_library_sees_them():
+    """The C ABI takes bare pointers, so the binding checks every caller buffer's
+    element count, dtype, host/device kind and device first: a bad one raises
+    ValueError and never reaches the library; a good one does (here the library
+    then refuses the NULL context with EINVAL, as no GPU is needed for that)."""
+    torch = pytest.importorskip("torch")
+    from paper_1107_4107_b300 import _lib
+    from paper_1107_4107_b300.api import ArnoldBatch, ArnoldEnsemble, _buf
+    n = 16
+    e = object.__new__(ArnoldEnsemble)
+    e.n, e.device, e._h = n, 0, None
+    bad = [lambda: e.indicator("chi", out=np.empty(n - 1)),                       # short
+           lambda: e.indicator("chi", out=np.empty(n, dtype=np.float32)),         # mistyped
+           lambda: e.indicator("class", out=np.empty(n)),                         # u8 kind into f64
+           lambda: e.indicator("V", out=np.empty(n)),                             # [3][n] kind
+           lambda: e.init_grid(4, 400.0, raw_out=np.empty((6, n))),               # host memory for a device write
+           lambda: e.init_grid(4, 400.0, raw_out=torch.empty((6, n), dtype=torch.float64)),
+           lambda: e.set_state_shell(np.zeros((3, n)), np.zeros((2, n)), 2, 400.0),
+           lambda: e.velocity_histogram(4, 8, out=np.zeros((4, 7), dtype=np.uint64)),
+           lambda: e.velocity_histogram(4, 8, out=np.zeros((4, 8))),
+           lambda: e.stats_arrays(np.zeros(n), np.zeros(n), np.zeros((3, n)), 1.0),   # device arrays only
+           lambda: e.grad(dL_dp=np.ones((3, n - 1))),
+           lambda: e.grad(dL_dp=np.ones((3, n)), out_x=np.empty((3, n)), out_p=np.empty((2, n))),
+           lambda: e.grad(dL_dp=np.ones((3, 2 * n))[:, ::2])]                         # not contiguous
+    for call in bad:
+        with pytest.raises(ValueError):
+            call()
+    good = [lambda: e.indicator("chi", out=np.empty(n)),
+            lambda: e.indicator("class", out=torch.empty(n, dtype=torch.uint8)),
+            lambda: e.indicator("V", out=np.empty((3, n))),
+            lambda: e.set_state_shell(np.zeros((3, n)), np.zeros((3, n)), 2, 400.0),
+            lambda: e.velocity_histogram(4, 8, out=np.zeros((4, 8), dtype=np.uint64)),
+            lambda: e.velocity_histogram(4, 8, out=torch.zeros((4, 8), dtype=torch.int64)),
+            lambda: e.grad(dL_dp=np.ones((3, n)))]
+    for call in good:
+        with pytest.raises(_lib.ArnoldError) as ex:
+            call()
+        assert ex.value.status == _lib.EINVAL
+    b = object.__new__(ArnoldBatch)
+    b.sets, b.device, b._h = [{"G": 4}], 0, None
+    with pytest.raises(ValueError):
+        b.indicator(0, "chi", out=np.empty(15))
+    with pytest.raises(_lib.ArnoldError):
+        b.indicator(0, "chi", out=np.empty(16))
+    assert _buf(np.empty((2, 3)), 6, ("float64",), "a", 0)[1] == _lib.HOST
