@@ -44,7 +44,8 @@ def tune_batch(sets, scheme: str = "yoshida6a", tangent: bool = True, use_cache:
     cache = {}
     if use_cache and os.path.exists(CACHE):
         try:
-            cache = json.load(open(CACHE))
+            with open(CACHE) as f:
+                cache = json.load(f)
         except ValueError:
             cache = {}
         if key in cache:
